@@ -1,0 +1,302 @@
+"""Throughput benchmark of the two-component colour-gradient LB step on GB300.
+
+One step = one pass of the whole hot path (streaming with boundary rules,
+node flips, moments, wall densities, colour gradient, local relaxation time,
+regularised collision, perturbation, recolouring) over the synthetic print
+lattice 512x128x128 (8.4M sites, D3Q19, FP32 storage and arithmetic), inputs
+resident in HBM. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent lattice per rank (replicas; the method has no
+exchange step between lattices), launched with torch.distributed.run.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2-component MLUPS & %HBM roofline; sweep sims/h, p50/p99 vs plain at same err"
+WORKLOAD = "print_512x128x128"
+REF_SAMPLE = "print_128x64x64"
+BYTES_PER_SITE = {"f32": 2 * 19 * 2 * 4, "f64": 2 * 19 * 2 * 8}  # read + write of the populations
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _fused_source_sha():
+    h = hashlib.sha256()
+    for f in ("lbm_fused.cu", "lbm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2102_02655_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_site():
+    """DRAM bytes per site update of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_fused_print_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_sha") == _fused_source_sha():
+            return float(d["dram_bytes_per_site"])
+    except Exception:
+        pass
+    return None
+
+
+def oracle_mlups(name, steps, threads=None):
+    """Time the FP64 CPU oracle as it stands on `steps` steps of a workload."""
+    import oracle as O
+    from paper_2102_02655_gb300 import inputs as I
+    wl = I.workload(name)
+    shape = wl["shape"]
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f64"), geom=wl["geom"], rheo=wl["rheo"])
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    ref.set_fields(rY, I.perturbed_ambient(shape, rB, seed=0))
+    ref.step(1)  # warm-up
+    t0 = time.perf_counter()
+    ref.step(steps)
+    dt = time.perf_counter() - t0
+    n = shape[0] * shape[1] * shape[2]
+    return n * steps / dt / 1e6, dt, n
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2102_02655_gb300 import inputs as I
+    shape = I.workload(REF_SAMPLE)["shape"]
+    n = shape[0] * shape[1] * shape[2]
+    if args.warmup:
+        oracle_mlups(REF_SAMPLE, args.warmup)
+    mlups, dt, _ = oracle_mlups(REF_SAMPLE, args.steps)
+    cores = O.threads_used()
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "D3Q19", "sites": 512 * 128 * 128},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%s (%d sites, same print parameters), %d steps per timed run"
+                                       % (REF_SAMPLE, n, args.steps)},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2102_02655_gb300 import build, inputs as I, lbm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    wl = I.workload(WORKLOAD)
+    shape = wl["shape"]
+    nsites = shape[0] * shape[1] * shape[2]
+    storage = wl["params"]["storage"]
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rB = I.perturbed_ambient(shape, rB, seed=rank)
+    lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path="fused", device=local)
+    lat.set_fields(rY, rB)
+    stream = lat.stream
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs, K steps, CUDA events on the stream
+    lat.profile(True)
+    launches0 = lat.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = lat.kernel_launches() - launches0
+    tm = lat.timings()
+    lat.profile(False)
+    ms = max_over_ranks(ms)
+    value = ws * nsites * args.steps / (ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (fused bulk kernel)
+    peak, peak_kind = _peaks()
+    bulk_ms_launch = tm["bulk_ms"] / max(1, tm["bulk_launches"])
+    bulk_sites_launch = tm["bulk_sites"] / max(1, tm["bulk_launches"])
+    bps = BYTES_PER_SITE[storage]
+    achieved = bps * bulk_sites_launch / (bulk_ms_launch * 1e-3) / 1e9
+    tps = _traffic_per_site()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": tps * bulk_sites_launch if tps is not None else None,
+            "kernel": "k_fused", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bps * bulk_sites_launch,
+            "kernel_ms_per_launch": bulk_ms_launch,
+            "kernel_share_of_step": tm["bulk_ms"] / max(1e-9, tm["bulk_ms"] + tm["plain_ms"]),
+            "box_kernels_ms_per_step": tm["plain_ms"] / max(1, tm["plain_groups"])}
+
+    # end to end through the C ABI with pinned host buffers: upload the
+    # initial fields, K steps, read back densities, velocity and diagnostics
+    npd = np.float32 if storage == "f32" else np.float64
+    tdt = torch.float32 if storage == "f32" else torch.float64
+    h_rY = torch.from_numpy(rY.astype(npd)).pin_memory()
+    h_rB = torch.from_numpy(rB.astype(npd)).pin_memory()
+    outs = [torch.empty(rY.shape, dtype=tdt).pin_memory() for _ in range(5)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.set_fields(h_rY.numpy(), h_rB.numpy())
+    lat.step(args.steps)
+    res = lat.fields(mask=lbm.LBM_FIELD_RHO_INK | lbm.LBM_FIELD_RHO_AMB | lbm.LBM_FIELD_U,
+                     out=[o.numpy() for o in outs])
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    esz = 4 if storage == "f32" else 8
+    e2e = {"value": ws * nsites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 2 * nsites * esz / args.steps,
+           "d2h_bytes_per_step": (5 * nsites * esz + 120) / args.steps,
+           "what": "per request: pinned H2D of rho_ink, rho_amb; K steps; D2H of rho_ink, rho_amb, u, diag"}
+    unstable = res["diag"]["unstable"]
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        cs = max(1, args.cpu_steps)
+        mlups, dt, n = oracle_mlups(WORKLOAD, cs)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": O.threads_used(), "kind": "oracle",
+               "sample": "%s full lattice (%d sites), %d steps after 1 untimed, %.1f s" % (WORKLOAD, n, cs, dt)}
+
+    lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "lattice": "D3Q19", "sites": nsites,
+                           "path": "fused bulk kernel + phase-by-phase nozzle box",
+                           "nozzle": "r 10, gap 20, head 0.01 l.u./step, power-law n 0.6, extrusion 0.02",
+                           "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * nsites * esz * 2 / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "unstable": unstable}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * lbm.h - C ABI of the GB300 library for the two-component regularised
+ * colour-gradient lattice Boltzmann step with a shear-thinning ink and a
+ * moving print head (Monteferrante et al., arXiv 2102.02655, Sec. II-III).
+ *
+ * One handle owns one lattice resident in device memory. All compute runs in
+ * the library's CUDA kernels on the handle's stream; the host side only
+ * validates arguments, computes the nozzle position per step and enqueues
+ * kernels.
+ *
+ * Conventions
+ *  - Lattice indices: site (x, y, z), x fastest, z the vertical axis (the
+ *    substrate is below z = 0, the open top above z = nz - 1). Field arrays
+ *    are [z][y][x] contiguous.
+ *  - Every call returns an lbm_status; nothing aborts. A failing call stores a
+ *    message readable with lbm_last_error. An LBM_ECUDA error is sticky: the
+ *    handle refuses further work and must be destroyed.
+ *  - Pointers named *_dev or passed with on_device = 1 are device pointers on
+ *    the handle's device; others are host pointers. Field values are double
+ *    for LBM_F64 storage and float otherwise.
+ *  - Calls on one handle must not overlap (one host thread at a time).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* invalid argument or configuration */
+    LBM_ENOMEM = 2,     /* device allocation failed */
+    LBM_ECUDA = 3,      /* CUDA runtime error (sticky) */
+    LBM_EUNSTABLE = 4,  /* a site saw a negative density or a NaN */
+    LBM_ETIMEOUT = 5,   /* a bounded host wait ran out */
+    LBM_ESTATE = 6      /* call out of order (e.g. lbm_step before geometry and rheology) */
+} lbm_status;
+
+/* Velocity set. D2Q9 is the paper's lattice (Sec. II A), laid in the x-z
+ * plane (ny must be 1); D3Q19 is the standard 3D set used for 3D lattices. */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_velset;
+
+/* Storage and arithmetic precision of the populations. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1 } lbm_storage;
+
+/* Execution path: PLAIN runs the phase-by-phase kernels over the whole
+ * lattice; FUSED runs the fused z-marching kernel over the bulk and the
+ * phase-by-phase kernels only in a box around the nozzle (D3Q19 only).
+ * AUTO picks FUSED where it applies. Both give the same result. */
+typedef enum { LBM_PATH_AUTO = 0, LBM_PATH_PLAIN = 1, LBM_PATH_FUSED = 2 } lbm_path;
+
+typedef enum { LBM_Z_PERIODIC = 0, LBM_Z_WALLS = 1 } lbm_zmode;
+typedef enum { LBM_TOP_OPEN = 0, LBM_TOP_WALL = 1 } lbm_topmode;
+typedef enum { LBM_NEWTONIAN = 0, LBM_CROSS = 1, LBM_POWER_LAW = 2 } lbm_law;
+
+/* Lattice and model constants (Sec. II A). */
+typedef struct {
+    int nx, ny, nz;
+    int velset;            /* lbm_velset */
+    int storage;           /* lbm_storage */
+    int path;              /* lbm_path */
+    double tau_ambient;    /* relaxation time of the Newtonian ambient (blue) fluid */
+    double rho0_ink, rho0_amb;    /* reference densities in the phase field rho^N */
+    double alpha_ink, alpha_amb;  /* phi_0 of each component (Eq. 7); <= 0 selects w_0 */
+    double A;              /* perturbation strength, sigma = 2 tau A / 9 (Eq. 10, 13) */
+    double beta;           /* recolouring parameter (Eq. 14-15) */
+    double zeta_ink, zeta_amb;    /* wall affinities in the fictitious densities (Eq. 18) */
+    double drag_gamma;     /* friction coefficient of the substrate drag (Eq. 29) */
+    double drag_height;    /* the drag acts closer than this to the substrate */
+    double body_force[3];  /* body acceleration (0 in the print runs) */
+    int device;            /* CUDA device ordinal */
+    void* cuda_stream;     /* cudaStream_t to enqueue on; NULL = a stream the library creates */
+    /* Optional device allocator. NULL alloc = cudaMalloc/cudaFree. The
+     * callbacks run inside lbm_create and lbm_destroy only. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+} lbm_config;
+
+/* Print-head geometry and boundaries (Sec. II B, Sec. III). */
+typedef struct {
+    int z_mode;            /* lbm_zmode: periodic in z, or substrate below and a top boundary */
+    int top_mode;          /* lbm_topmode: open (anti-bounce-back, Eq. 28) or a moving lid */
+    int nozzle;            /* 1: annular nozzle present (requires LBM_Z_WALLS) */
+    double head_pos[2];    /* nozzle axis (x, y) at step 0, lattice units */
+    double head_vel[2];    /* nozzle velocity v_nozzle in the x-y plane (Eq. 26) */
+    double r_inner;        /* inner radius of the nozzle wall */
+    double wall_thickness; /* the wall spans r_inner <= r <= r_inner + wall_thickness */
+    int gap;               /* lowest z of the nozzle wall; the substrate is at z = -1/2 */
+    double u_ink;          /* extrusion speed in the head frame, along -z (Eq. 27) */
+    double top_vel[3];     /* lid velocity when top_mode = LBM_TOP_WALL */
+    double rho_top_amb;    /* ambient density imposed at the open top (Eq. 28) */
+} lbm_geometry;
+
+/* Ink rheology (Eq. 23-25): kinematic viscosity of the ink as a function of
+ * the shear rate from the implicit equation Eq. 24. */
+typedef struct {
+    int law;               /* lbm_law */
+    double nu0, nu_inf, lambda, n;  /* Cross: nu = nu_inf + (nu0 - nu_inf)/(1 + (lambda gdot)^n) */
+    double K;              /* power law: nu = K gdot^(n-1) */
+    double tau_min, tau_max;        /* clamps of the ink and mixture relaxation times */
+    double tol;            /* relative tolerance of the shear-rate iteration (<= 0: default) */
+    int max_iter;          /* iteration cap (<= 0: default 60) */
+} lbm_rheology;
+
+/* Diagnostics, accumulated in FP64 on the device. */
+typedef struct {
+    double mass[2];        /* sum of rho^ink, rho^amb over fluid nodes at the last step */
+    double momentum[3];    /* sum of rho u (physical velocity) at the last step */
+    double bc_flux[2];     /* cumulative mass entering minus leaving at boundary links */
+    double created[2];     /* cumulative mass of nodes uncovered by the nozzle */
+    double destroyed[2];   /* cumulative mass of nodes covered by the nozzle */
+    long long step;        /* steps since lbm_set_geometry */
+    int unstable;          /* 1 if any site saw a negative density or a NaN */
+} lbm_diag;
+
+/* Field selection bits for lbm_fields; the buffers are taken in this order. */
+enum {
+    LBM_FIELD_RHO_INK = 1 << 0,  /* rho^Y (Eq. 2) */
+    LBM_FIELD_RHO_AMB = 1 << 1,  /* rho^B */
+    LBM_FIELD_U = 1 << 2,        /* physical velocity, 3 arrays ux, uy, uz (Eq. 3) */
+    LBM_FIELD_NU = 1 << 3,       /* mixture kinematic viscosity c_s^2 (tau - 1/2) (Eq. 17) */
+    LBM_FIELD_P = 1 << 4,        /* pressure sum_k p^k (Eq. 9) */
+    LBM_FIELD_PHI = 1 << 5,      /* phase field rho^N */
+    LBM_FIELD_SOLID = 1 << 6     /* 1 on nozzle nodes, 0 on fluid nodes */
+};
+
+/* Create a lattice (Sec. II A constants). Allocates the device state through
+ * cfg->alloc (or cudaMalloc). Returns LBM_EINVAL for bad sizes/values,
+ * LBM_ENOMEM if an allocation fails. *out is NULL on failure. */
+lbm_status lbm_create(const lbm_config* cfg, struct lbm_handle** out);
+
+/* Set the print-head geometry and boundaries, reset the step counter and the
+ * diagnostics, and initialise the state of Sec. III: the nozzle interior
+ * above the gap filled with ink, ambient fluid elsewhere, all at rest, with
+ * equilibrium populations. LBM_EINVAL for an inconsistent geometry. */
+lbm_status lbm_set_geometry(struct lbm_handle* h, const lbm_geometry* g);
+
+/* Set the ink rheology (Eq. 23-25). LBM_EINVAL if tau_min <= 1/2 or
+ * tau_max < tau_min or the law's parameters are out of range. */
+lbm_status lbm_set_ink_rheology(struct lbm_handle* h, const lbm_rheology* r);
+
+/* Replace the state by equilibrium populations of the given densities and
+ * velocity (u = NULL: at rest) on every fluid node; solid nodes are ignored.
+ * rho_ink, rho_amb: nx*ny*nz values; u: 3 arrays (ux, uy, uz) back to back.
+ * on_device selects device or host pointers. Resets the ledger. */
+lbm_status lbm_set_fields(struct lbm_handle* h, const void* rho_ink, const void* rho_amb,
+                          const void* u, int on_device);
+
+/* Enqueue nsteps time steps (Eq. 1) on the handle's stream and return. The
+ * macroscopic fields of the last step are kept for lbm_fields. LBM_ESTATE if
+ * geometry or rheology are missing. */
+lbm_status lbm_step(struct lbm_handle* h, int nsteps);
+
+/* Copy the fields selected by mask (LBM_FIELD_*) of the last completed step
+ * into dst[0..] (one nx*ny*nz buffer per field, three for LBM_FIELD_U), on the
+ * device or host per dst_on_device, and fill *diag if not NULL. Waits for the
+ * stream. Returns LBM_EUNSTABLE (after copying) if the unstable flag is set. */
+lbm_status lbm_fields(struct lbm_handle* h, unsigned mask, void* const* dst, int dst_on_device,
+                      lbm_diag* diag);
+
+/* Wait for all enqueued work, giving up after timeout_ms (<= 0: no limit);
+ * LBM_ETIMEOUT if it did not finish in time. */
+lbm_status lbm_sync(struct lbm_handle* h, int timeout_ms);
+
+/* Release the lattice and its device memory. NULL is accepted. */
+void lbm_destroy(struct lbm_handle* h);
+
+/* Message of the last failing call on h (or of the last lbm_create failure
+ * when h is NULL). Valid until the next call on h. */
+const char* lbm_last_error(const struct lbm_handle* h);
+
+/* Number of kernel launches enqueued on h since its creation. */
+long long lbm_kernel_launches(const struct lbm_handle* h);
+
+/* Device time of the library's kernels, measured with CUDA events recorded
+ * on the handle's stream around the fused bulk kernel and around the group of
+ * phase-by-phase kernels of every step while profiling is on. */
+typedef struct {
+    double bulk_ms;            /* summed duration of the fused bulk kernel launches */
+    double plain_ms;           /* summed duration of the phase-by-phase kernel groups */
+    long long bulk_launches, plain_groups;
+    long long bulk_sites;      /* site updates done by the fused bulk kernel */
+    long long plain_sites;     /* site updates done by the phase-by-phase kernels */
+} lbm_timing;
+
+/* Turn event timing on (1) or off (0); turning it on clears the totals. */
+lbm_status lbm_profile(struct lbm_handle* h, int enable);
+
+/* Wait for the stream and return the totals since profiling was turned on. */
+lbm_status lbm_timings(struct lbm_handle* h, lbm_timing* out);
+
+typedef struct lbm_handle lbm_handle;
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

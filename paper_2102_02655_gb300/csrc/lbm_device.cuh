@@ -1,0 +1,562 @@
+// Device-side building blocks of the two-component regularised colour-gradient
+// lattice Boltzmann step (Monteferrante et al., arXiv 2102.02655, Sec. II):
+// lattice constants, the nozzle template in fixed point, streaming with the
+// boundary rules, and the collision at one site. Shared by the phase-by-phase
+// kernels and the fused bulk kernel so that both compute the same arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cglbm {
+
+constexpr int kMaxQ = 19;
+
+// ---------------------------------------------------------------------------
+// Velocity sets. Direction pairs (1,2), (3,4), ... are opposite.
+// ---------------------------------------------------------------------------
+
+// D3Q19: rest, 6 axis links (w = 1/18), 12 face diagonals (w = 1/36).
+struct D3Q19 {
+    static constexpr int Q = 19;
+    static constexpr bool kPlanar = false;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr int shell(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    // Perturbation coefficients (Eq. 10) for D3Q19: B_i = w_i (|c_i|^2 - 2/3),
+    // the one choice proportional to w_i and quadratic in |c_i| that keeps the
+    // two properties of the paper's D2Q9 values: sum_i B_i = c_s^2 and
+    // sum_i B_i c_i c_i = I/3.
+    __host__ __device__ static constexpr double B(int i) {
+        return i == 0 ? -2.0 / 9.0 : (i <= 6 ? 1.0 / 54.0 : 1.0 / 27.0);
+    }
+    // phi^k_i share of the moving links (Eq. 7 generalised): (1 - alpha)/12 on
+    // axes, (1 - alpha)/24 on diagonals.
+    __host__ __device__ static constexpr double phi_share(int i) {
+        return i == 0 ? 0.0 : (i <= 6 ? 1.0 / 12.0 : 1.0 / 24.0);
+    }
+    __host__ __device__ static constexpr double inv_norm(int i) {
+        return i == 0 ? 0.0 : (i <= 6 ? 1.0 : 0.70710678118654752440);
+    }
+};
+
+// D2Q9 of Sec. II A, laid in the x-z plane: rest (4/9), 4 axis links (1/9),
+// 4 diagonals (1/36), B_i = -4/27, 2/27, 5/108 as printed after Eq. 12.
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr bool kPlanar = true;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 0, 1}, {0, 0, -1},
+                                 {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr int shell(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr double B(int i) {
+        return i == 0 ? -4.0 / 27.0 : (i <= 4 ? 2.0 / 27.0 : 5.0 / 108.0);
+    }
+    // Eq. 7: (1 - alpha)/5 on axes, (1 - alpha)/20 on diagonals
+    __host__ __device__ static constexpr double phi_share(int i) {
+        return i == 0 ? 0.0 : (i <= 4 ? 1.0 / 5.0 : 1.0 / 20.0);
+    }
+    __host__ __device__ static constexpr double inv_norm(int i) {
+        return i == 0 ? 0.0 : (i <= 4 ? 1.0 : 0.70710678118654752440);
+    }
+};
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+enum { kZPeriodic = 0, kZWalls = 1 };
+enum { kTopOpen = 0, kTopWall = 1 };
+enum { kLawNewtonian = 0, kLawCross = 1, kLawPower = 2 };
+
+// accumulator slots (FP64, device)
+enum { kAccBc = 0, kAccDestroyed = 2, kAccCreated = 4, kAccMass = 6, kAccMom = 8, kAccN = 16 };
+// field planes written on the last step of an lbm_step call
+enum { kFRhoInk = 0, kFRhoAmb, kFUx, kFUy, kFUz, kFNu, kFP, kFPhi, kFSolid, kNFields };
+
+// An axis-aligned region of sites with periodic x, y: x = (x0 + i) mod nx for
+// 0 <= i < wx, likewise y, and z0 <= z < z1.
+struct Region {
+    int x0, wx, y0, wy, z0, z1;
+};
+
+// Everything a kernel needs for one step. Passed by value.
+template <typename real>
+struct StepArgs {
+    int nx, ny, nz;
+    long long N;       // sites
+    long long plane;   // nx * ny
+    int z_mode, top_mode, nozzle, gap;
+    // nozzle axis at step n-1 (index 0) and step n (index 1), in 2^-20 lattice
+    // units, reduced into [0, period)
+    long long hx[2], hy[2];
+    long long rin2, rout2, px, py;  // squared radii (fixed point^2), periods
+    real vn[3];        // nozzle velocity (moving-wall rule and node creation)
+    real uin[3];       // inlet velocity u_ink + v_nozzle (Eq. 27)
+    real utop[3];      // lid velocity
+    real rho_top;      // imposed ambient density at the open top
+    real rho0[2], zeta[2], A, beta, nuB, g[3], drag_gamma, drag_height;
+    real phi[2][kMaxQ];
+    real pfac[2];      // p^k = pfac[k] rho^k (Eq. 9)
+    int law, max_iter;
+    real nu0, nu_inf, lambda, n_exp, K, tau_min, tau_max, tol;
+    // state
+    const real* fin;
+    real* fout;
+    real* rho_cur;         // (nz + 2) planes, z = -1 .. nz
+    const real* rho_prev;
+    const real* u_prev;    // physical velocity of the last two planes, 3 x 2 x plane
+    real* u_cur;
+    real* fields;          // kNFields x N
+    double* acc;
+    int* flags;
+    int write_fields;
+    Region box;            // nozzle box (fused path); wx = 0 when unused
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int wrapn(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+template <typename real>
+__device__ __forceinline__ real clampr(real v, real lo, real hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+template <typename real>
+__device__ __forceinline__ long long ridx(const StepArgs<real>& p, int x, int y, int z) {
+    return (long long)(z + 1) * p.plane + (long long)y * p.nx + x;
+}
+
+template <typename real>
+__device__ __forceinline__ long long sidx(const StepArgs<real>& p, int x, int y, int z) {
+    return (long long)z * p.plane + (long long)y * p.nx + x;
+}
+
+// ---------------------------------------------------------------------------
+// Nozzle template (Sec. II B), fixed point
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ long long near_image(long long d, long long period) {
+    // d in (-period, period) because the head coordinate is reduced on the host
+    if (2 * d >= period) d -= period;
+    else if (2 * d < -period) d += period;
+    return d;
+}
+
+template <typename real>
+__device__ __forceinline__ long long axis_d2(const StepArgs<real>& p, int x, int y, int which) {
+    long long dx = near_image((long long)x * 1048576LL - p.hx[which], p.px);
+    long long dy = near_image((long long)y * 1048576LL - p.hy[which], p.py);
+    return dx * dx + dy * dy;
+}
+
+// nozzle wall node (z >= gap, r_in <= r <= r_out) on the geometry of step n-1 (0) or n (1)
+template <typename real>
+__device__ __forceinline__ bool solid_at(const StepArgs<real>& p, int x, int y, int z, int which) {
+    if (!p.nozzle || z < p.gap) return false;
+    long long d2 = axis_d2(p, x, y, which);
+    return d2 >= p.rin2 && d2 <= p.rout2;
+}
+
+// ---------------------------------------------------------------------------
+// Equilibrium (Eq. 6, with 2 c_s^4 under (c.u)^2)
+// ---------------------------------------------------------------------------
+
+template <class VS, typename real>
+__device__ __forceinline__ real feq_i(real phi_i, int i, real rho, real ux, real uy, real uz, real uu) {
+    const real cu = (real)VS::c(i, 0) * ux + (real)VS::c(i, 1) * uy + (real)VS::c(i, 2) * uz;
+    const real w = (real)VS::w(i);
+    return rho * (phi_i + w * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu));
+}
+
+// ---------------------------------------------------------------------------
+// Streaming with the boundary rules (Eq. 1, 26-28), full generality.
+// Pulls the populations of fluid site (x, y, z) of the step-(n-1) geometry.
+// bc[k] accumulates the mass change of the boundary links.
+// ---------------------------------------------------------------------------
+
+template <class VS, typename real>
+__device__ __forceinline__ real wall_density(const StepArgs<real>& p, int k, int x, int y, int z, int i,
+                                             long long s_self) {
+    // Eq. 26: density at the wall by quadratic extrapolation along +c_i from
+    // x (distance 1/2), x + c_i (3/2), x + 2 c_i (5/2), using the step-(n-1)
+    // densities; falls back to the node's own density if either is not fluid.
+    const real r0 = p.rho_prev[(long long)k * (p.N + 2 * p.plane) + s_self + p.plane];
+    const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
+    const int x2 = wrapn(x + 2 * VS::c(i, 0), p.nx), y2 = wrapn(y + 2 * VS::c(i, 1), p.ny);
+    int z1 = z + VS::c(i, 2), z2 = z + 2 * VS::c(i, 2);
+    if (p.z_mode == kZPeriodic) {
+        z1 = wrapn(z1, p.nz);
+        z2 = wrapn(z2, p.nz);
+    } else if (z1 < 0 || z1 >= p.nz || z2 < 0 || z2 >= p.nz) {
+        return r0;
+    }
+    if (solid_at(p, x1, y1, z1, 0) || solid_at(p, x2, y2, z2, 0)) return r0;
+    const long long off = (long long)k * (p.N + 2 * p.plane);
+    const real r1 = p.rho_prev[off + ridx(p, x1, y1, z1)];
+    const real r2 = p.rho_prev[off + ridx(p, x2, y2, z2)];
+    return (real(15) * r0 - real(10) * r1 + real(3) * r2) * real(0.125);
+}
+
+// index of the velocity of the top two planes (z = nz-2, nz-1)
+template <typename real>
+__device__ __forceinline__ long long utop_idx(const StepArgs<real>& p, int a, int x, int y, int z) {
+    return ((long long)a * 2 + (z - (p.nz - 2))) * p.plane + (long long)y * p.nx + x;
+}
+
+template <class VS, typename real>
+__device__ __forceinline__ void anti_bb_velocity(const StepArgs<real>& p, int x, int y, int z, int i, real uw[3]) {
+    // Eq. 28: half-way velocity by second-order extrapolation
+    // 1.5 u(x) - 0.5 u(x + c_i), step n-1 values; u(x) alone if x + c_i is not fluid
+    for (int a = 0; a < 3; ++a) uw[a] = p.u_prev[utop_idx(p, a, x, y, z)];
+    const int z1 = z + VS::c(i, 2);
+    if (z1 < 0 || z1 < p.nz - 2) return;
+    const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
+    if (solid_at(p, x1, y1, z1, 0)) return;
+    for (int a = 0; a < 3; ++a) uw[a] = real(1.5) * uw[a] - real(0.5) * p.u_prev[utop_idx(p, a, x1, y1, z1)];
+}
+
+enum { kLinkFluid = 0, kLinkRest, kLinkMoving, kLinkOpen };
+
+template <class VS, typename real>
+__device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, int z, int i, long long* src,
+                                        real uw[3]) {
+    const int sx = wrapn(x - VS::c(i, 0), p.nx), sy = wrapn(y - VS::c(i, 1), p.ny);
+    int sz = z - VS::c(i, 2);
+    uw[0] = uw[1] = uw[2] = real(0);
+    if (p.z_mode == kZPeriodic) {
+        *src = sidx(p, sx, sy, wrapn(sz, p.nz));
+        return kLinkFluid;
+    }
+    if (sz < 0) return kLinkRest;  // substrate: resting wall half-way below z = 0
+    if (sz >= p.nz) {
+        if (p.top_mode == kTopWall) {
+            uw[0] = p.utop[0]; uw[1] = p.utop[1]; uw[2] = p.utop[2];
+            return kLinkMoving;
+        }
+        if (p.nozzle) {
+            const long long d2 = axis_d2(p, sx, sy, 0);
+            if (d2 >= p.rin2 && d2 <= p.rout2) {
+                uw[0] = p.vn[0]; uw[1] = p.vn[1]; uw[2] = p.vn[2];
+                return kLinkMoving;
+            }
+            if (d2 < p.rin2) {  // inlet, Eq. 27
+                uw[0] = p.uin[0]; uw[1] = p.uin[1]; uw[2] = p.uin[2];
+                return kLinkMoving;
+            }
+        }
+        return kLinkOpen;
+    }
+    if (solid_at(p, sx, sy, sz, 0)) {
+        uw[0] = p.vn[0]; uw[1] = p.vn[1]; uw[2] = p.vn[2];
+        return kLinkMoving;
+    }
+    *src = sidx(p, sx, sy, sz);
+    return kLinkFluid;
+}
+
+template <class VS, typename real>
+__device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int y, int z, real f[2][VS::Q],
+                                             real bc[2]) {
+    const long long s = sidx(p, x, y, z);
+#pragma unroll
+    for (int i = 0; i < VS::Q; ++i) {
+        long long src = 0;
+        real uw[3];
+        const int kind = classify<VS>(p, x, y, z, i, &src, uw);
+        const int ib = opp(i);
+        if (kind == kLinkFluid) {
+            f[0][i] = p.fin[(long long)i * p.N + src];
+            f[1][i] = p.fin[(long long)(VS::Q + i) * p.N + src];
+            continue;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const real own = p.fin[(long long)(k * VS::Q + ib) * p.N + s];
+            real v;
+            if (kind == kLinkRest) {
+                v = own;
+            } else if (kind == kLinkMoving) {
+                const real rw = wall_density<VS>(p, k, x, y, z, i, s);
+                const real ucb = -((real)VS::c(i, 0) * uw[0] + (real)VS::c(i, 1) * uw[1] + (real)VS::c(i, 2) * uw[2]);
+                v = own - real(2) * (real)VS::w(ib) * rw * ucb * real(3);
+            } else {
+                real u2[3];
+                anti_bb_velocity<VS>(p, x, y, z, i, u2);
+                const real rw = k == 0 ? real(0) : p.rho_top;
+                const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
+                const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+                v = -own + real(2) * rw * (p.phi[k][ib] + (real)VS::w(ib) * (real(4.5) * cu * cu - real(1.5) * uu));
+            }
+            f[k][i] = v;
+            bc[k] += v - own;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Local relaxation time (Eq. 17, 23-25)
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__device__ __forceinline__ real rpow(real a, real b);
+template <>
+__device__ __forceinline__ double rpow<double>(double a, double b) { return pow(a, b); }
+template <>
+__device__ __forceinline__ float rpow<float>(float a, float b) { return powf(a, b); }
+
+template <typename real>
+__device__ __forceinline__ real rsqrt_(real a);
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double a) { return sqrt(a); }
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float a) { return sqrtf(a); }
+
+// tau of the ink law at shear rate g (unclamped) and d tau / d g
+template <typename real>
+__device__ __forceinline__ void tau_law(const StepArgs<real>& p, real g, real* t, real* dt) {
+    if (p.law == kLawCross) {
+        const real xg = rpow(p.lambda * g, p.n_exp);
+        const real inv = real(1) / (real(1) + xg);
+        const real nu = p.nu_inf + (p.nu0 - p.nu_inf) * inv;
+        *t = real(0.5) + real(3) * nu;
+        *dt = g > real(0) ? -real(3) * (p.nu0 - p.nu_inf) * p.n_exp * xg * inv * inv / g : real(0);
+    } else {  // power law
+        const real nu = p.K * rpow(g, p.n_exp - real(1));
+        *t = real(0.5) + real(3) * nu;
+        *dt = real(3) * (p.n_exp - real(1)) * nu / g;
+    }
+}
+
+// tau of the ink at zero shear rate (clamped)
+template <typename real>
+__device__ __forceinline__ real tau_zero_shear(const StepArgs<real>& p) {
+    if (p.law == kLawPower) {
+        if (p.n_exp < real(1)) return p.tau_max;
+        if (p.n_exp > real(1)) return p.tau_min;
+        return clampr(real(0.5) + real(3) * p.K, p.tau_min, p.tau_max);
+    }
+    return clampr(real(0.5) + real(3) * p.nu0, p.tau_min, p.tau_max);
+}
+
+// Root of g tau_Y(g) = S / (rho_Y c_s^2) (Eq. 24-25) by Newton's method kept
+// inside the bracket [s / tau_max, s / tau_min] (bisection when a step leaves
+// it); stops when the relative step is below tol. Returns the clamped tau_Y.
+template <typename real>
+__device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, real rhoY, real rho) {
+    if (p.law == kLawNewtonian) return clampr(real(0.5) + real(3) * p.nu0, p.tau_min, p.tau_max);
+    if (!(rhoY > real(1e-12) * rho) || !(S > real(0))) return tau_zero_shear(p);
+    const real s = real(3) * S / rhoY;
+    real lo = s / p.tau_max, hi = s / p.tau_min;
+    real t, dt;
+    tau_law(p, lo, &t, &dt);
+    if (t >= p.tau_max) return p.tau_max;  // root on the tau_max branch
+    tau_law(p, hi, &t, &dt);
+    if (t <= p.tau_min) return p.tau_min;  // root on the tau_min branch
+    real g = lo;
+    for (int it = 0; it < p.max_iter; ++it) {
+        tau_law(p, g, &t, &dt);
+        if (t > p.tau_max) { t = p.tau_max; dt = real(0); }
+        else if (t < p.tau_min) { t = p.tau_min; dt = real(0); }
+        const real h = g * t - s;
+        if (h < real(0)) lo = g; else hi = g;
+        real gn = g - h / (t + g * dt);
+        if (!(gn > lo && gn < hi)) gn = real(0.5) * (lo + hi);
+        const real step = gn - g;
+        g = gn;
+        if (fabs(step) <= p.tol * g) break;
+    }
+    tau_law(p, g, &t, &dt);
+    return clampr(t, p.tau_min, p.tau_max);
+}
+
+// ---------------------------------------------------------------------------
+// Collision at one fluid site (Eq. 4-20, 29).
+//   f[k][i]: populations after streaming, replaced by the post-collision ones.
+//   nb(i, &cY, &cB, &rn): colour fractions rho_Y/rho, rho_B/rho and phase
+//   field rho^N of the neighbour x + c_i (fluid, wall or ghost node).
+//   zdist: distance to the substrate (drag zone), < 0 when there is none.
+// Outputs the physical velocity and tau for the fields.
+// ---------------------------------------------------------------------------
+
+template <typename real>
+struct SiteOut {
+    real rhoY, rhoB, u[3], tau, rn;
+};
+
+template <typename real>
+__device__ __forceinline__ real phase_field(const StepArgs<real>& p, real rY, real rB) {
+    const real aY = rY / p.rho0[0], aB = rB / p.rho0[1];
+    return (aY - aB) / (aY + aB);
+}
+
+template <class VS, typename real, typename Nb>
+__device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q], const Nb& nb, real zdist,
+                                        SiteOut<real>* so) {
+    constexpr int Q = VS::Q;
+    // moments (Eq. 2-3)
+    real rY = 0, rB = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rY += f[0][i];
+        rB += f[1][i];
+        const real ft = f[0][i] + f[1][i];
+        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? ft : -ft;
+        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? ft : -ft;
+        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? ft : -ft;
+    }
+    const real rho = rY + rB;
+    const real irho = real(1) / rho;
+    const real ux = mx * irho, uy = my * irho, uz = mz * irho;
+    const real uu = ux * ux + uy * uy + uz * uz;
+    const real cY0 = rY / rho, cB0 = rB / rho;
+    const real rn0 = phase_field(p, rY, rB);
+
+    // colour-gradient force (Eq. 11) and grad rho^N by the isotropic stencil
+    // (Eq. 12) in central-difference form, exactly zero on uniform fields
+    real gY[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gN[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        real cY, cB, rn;
+        nb(i, &cY, &cB, &rn);
+        const real w = (real)VS::w(i);
+        const real dY = w * (cY - cY0), dB = w * (cB - cB0), dN = w * (rn - rn0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (VS::c(i, a) > 0) { gY[a] += dY; gB[a] += dB; gN[a] += dN; }
+            else if (VS::c(i, a) < 0) { gY[a] -= dY; gB[a] -= dB; gN[a] -= dN; }
+        }
+    }
+    real F[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        gY[a] *= real(3); gB[a] *= real(3); gN[a] *= real(3);
+        F[a] = cB0 * gY[a] - cY0 * gB[a];
+    }
+    const real Fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    const real gNn = rsqrt_(gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2]);
+
+    // non-equilibrium stress of each component (Eq. 20):
+    // Pi^neq = sum_i f c c - rho_k (pfac_k I + u u)
+    real P[2][6];  // xx yy zz xy xz yz
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        real sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const real v = f[k][i];
+            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+            if (cx) sxx += v;
+            if (cy) syy += v;
+            if (cz) szz += v;
+            if (cx && cy) sxy += (cx == cy) ? v : -v;
+            if (cx && cz) sxz += (cx == cz) ? v : -v;
+            if (cy && cz) syz += (cy == cz) ? v : -v;
+        }
+        const real rk = k == 0 ? rY : rB;
+        const real pk = p.pfac[k] * rk;
+        P[k][0] = sxx - (pk + rk * ux * ux);
+        P[k][1] = syy - (pk + rk * uy * uy);
+        P[k][2] = szz - (pk + rk * uz * uz);
+        P[k][3] = sxy - rk * ux * uy;
+        P[k][4] = sxz - rk * ux * uz;
+        P[k][5] = syz - rk * uy * uz;
+        if (VS::kPlanar) { P[k][1] = 0; P[k][3] = 0; P[k][5] = 0; }
+    }
+
+    // local relaxation time: ink viscosity from Eq. 24-25, harmonic mixing
+    // by mass fraction (Eq. 17), clamp
+    const real S = rsqrt_(P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2] +
+                          real(2) * (P[0][3] * P[0][3] + P[0][4] * P[0][4] + P[0][5] * P[0][5]));
+    const real tauY = solve_tau_ink(p, S, rY, rho);
+    const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
+    const real inv_nu = cY0 / nuY + cB0 / p.nuB;
+    const real tau = clampr(real(0.5) + real(3) / inv_nu, p.tau_min, p.tau_max);
+    const real om = real(1) - real(1) / tau;
+
+    // body force and drag by the exact difference method (Eq. 29)
+    real Fb[3] = {rho * p.g[0], rho * p.g[1], rho * p.g[2]};
+    if (p.drag_gamma != real(0) && zdist >= real(0) && zdist < p.drag_height) {
+        Fb[0] -= p.drag_gamma * rY * ux;
+        Fb[1] -= p.drag_gamma * rY * uy;
+        Fb[2] -= p.drag_gamma * rY * uz;
+    }
+    const bool forced = (Fb[0] != real(0)) || (Fb[1] != real(0)) || (Fb[2] != real(0));
+    const real vx = ux + Fb[0] * irho, vy = uy + Fb[1] * irho, vz = uz + Fb[2] * irho;
+    const real vv = vx * vx + vy * vy + vz * vz;
+
+    // perturbation (Eq. 10) once on the total, recolouring (Eq. 14-16)
+    const bool pert = gNn > real(0) && Fn2 > real(0);
+    const real pA = pert ? real(0.5) * p.A * gNn : real(0);
+    const real iFn2 = pert ? real(1) / Fn2 : real(0);
+    const real rec = gNn > real(0) ? p.beta * rY * rB * irho * irho / gNn : real(0);
+    const real trY = P[0][0] + P[0][1] + P[0][2], trB = P[1][0] + P[1][1] + P[1][2];
+
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        const real w = (real)VS::w(i);
+        const real cu = cx * ux + cy * uy + cz * uz;
+        // regularised BGK: f^eq + (1 - 1/tau) w/(2 c_s^4) (c.Pi.c - c_s^2 tr Pi)
+        real qY = cx * cx * P[0][0] + cy * cy * P[0][1] + cz * cz * P[0][2] +
+                  real(2) * (cx * cy * P[0][3] + cx * cz * P[0][4] + cy * cz * P[0][5]) - trY * real(1.0 / 3.0);
+        real qB = cx * cx * P[1][0] + cy * cy * P[1][1] + cz * cz * P[1][2] +
+                  real(2) * (cx * cy * P[1][3] + cx * cz * P[1][4] + cy * cz * P[1][5]) - trB * real(1.0 / 3.0);
+        const real base = real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu;
+        real fY = rY * (p.phi[0][i] + w * base) + om * w * real(4.5) * qY;
+        real fB = rB * (p.phi[1][i] + w * base) + om * w * real(4.5) * qB;
+        if (forced) {
+            const real cv = cx * vx + cy * vy + cz * vz;
+            const real dbase = w * ((real(3) * cv + real(4.5) * cv * cv - real(1.5) * vv) - base);
+            fY += rY * dbase;
+            fB += rB * dbase;
+        }
+        real fs = fY + fB;
+        if (pert) {
+            const real Fc = cx * F[0] + cy * F[1] + cz * F[2];
+            fs += pA * (w * Fc * Fc * iFn2 - (real)VS::B(i));
+        }
+        real gcol = real(0);
+        if (i != 0) {
+            const real cg = (cx * gN[0] + cy * gN[1] + cz * gN[2]) * (real)VS::inv_norm(i);
+            gcol = rec * cg * (rY * p.phi[0][i] + rB * p.phi[1][i]);
+        }
+        f[0][i] = cY0 * fs + gcol;
+        f[1][i] = cB0 * fs - gcol;
+    }
+
+    so->rhoY = rY;
+    so->rhoB = rB;
+    so->u[0] = ux + real(0.5) * Fb[0] * irho;
+    so->u[1] = uy + real(0.5) * Fb[1] * irho;
+    so->u[2] = uz + real(0.5) * Fb[2] * irho;
+    so->tau = tau;
+    so->rn = rn0;
+}
+
+// unstable: NaN, non-positive total density, or a clearly negative component
+template <typename real>
+__device__ __forceinline__ bool unstable_site(real rY, real rB) {
+    const real rho = rY + rB;
+    return !(rho > real(0)) || rY < real(-1e-3) * rho || rB < real(-1e-3) * rho;
+}
+
+}  // namespace cglbm

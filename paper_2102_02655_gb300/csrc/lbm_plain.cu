@@ -1,0 +1,366 @@
+// Phase-by-phase kernels: the direct form of one time step, used over the
+// whole lattice (plain path) or only in the box around the nozzle (fused
+// path). Order of a step (Sec. II A-B): stream on the step-(n-1) geometry with
+// the boundary rules, delete/create the nodes the nozzle covers/uncovers, take
+// moments, fill the fictitious wall densities, then collide.
+#include "lbm_launch.h"
+
+namespace cglbm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool region_site(const Region& r, long long t, int nx, int ny, int* x, int* y, int* z) {
+    const long long nxy = (long long)r.wx * r.wy;
+    if (t >= nxy * (r.z1 - r.z0)) return false;
+    const int zz = (int)(t / nxy);
+    const long long rem = t - (long long)zz * nxy;
+    const int j = (int)(rem / r.wx);
+    const int i = (int)(rem - (long long)j * r.wx);
+    *x = wrapn(r.x0 + i, nx);
+    *y = wrapn(r.y0 + j, ny);
+    *z = r.z0 + zz;
+    return true;
+}
+
+__device__ __forceinline__ bool in_region(const Region& r, int x, int y, int z, int nx, int ny) {
+    if (z < r.z0 || z >= r.z1) return false;
+    int dx = x - r.x0;
+    if (dx < 0) dx += nx;
+    int dy = y - r.y0;
+    if (dy < 0) dy += ny;
+    return dx < r.wx && dy < r.wy;
+}
+
+// sum over the warp, one atomic per warp
+__device__ __forceinline__ void warp_add(double* dst, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+__host__ __device__ inline long long region_sites(const Region& r) { return (long long)r.wx * r.wy * (r.z1 - r.z0); }
+
+inline int blocks_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// 1. stream + densities (post-streaming) of every fluid node of step n-1 in R2
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_stream_density(StepArgs<real> p, Region R2, Region R) {
+    const long long comp = p.N + 2 * p.plane;
+    double bc0 = 0, bc1 = 0, de0 = 0, de1 = 0;
+    const long long total = region_sites(R2);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        region_site(R2, t, p.nx, p.ny, &x, &y, &z);
+        if (solid_at(p, x, y, z, 0)) continue;
+        real f[2][VS::Q];
+        real bc[2] = {real(0), real(0)};
+        pull_general<VS>(p, x, y, z, f, bc);
+        real rY = 0, rB = 0;
+#pragma unroll
+        for (int i = 0; i < VS::Q; ++i) { rY += f[0][i]; rB += f[1][i]; }
+        const long long r = ridx(p, x, y, z);
+        p.rho_cur[r] = rY;
+        p.rho_cur[comp + r] = rB;
+        if (in_region(R, x, y, z, p.nx, p.ny)) {
+            bc0 += (double)bc[0];
+            bc1 += (double)bc[1];
+            if (solid_at(p, x, y, z, 1)) { de0 += (double)rY; de1 += (double)rB; }
+        }
+    }
+    warp_add(p.acc + kAccBc, bc0);
+    warp_add(p.acc + kAccBc + 1, bc1);
+    warp_add(p.acc + kAccDestroyed, de0);
+    warp_add(p.acc + kAccDestroyed + 1, de1);
+}
+
+// 2. nodes the nozzle uncovered: mean density of the neighbours that are fluid
+//    at both steps (Sec. II B)
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R1, Region R) {
+    const long long comp = p.N + 2 * p.plane;
+    double c0 = 0, c1 = 0;
+    const long long total = region_sites(R1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        region_site(R1, t, p.nx, p.ny, &x, &y, &z);
+        if (!(solid_at(p, x, y, z, 0) && !solid_at(p, x, y, z, 1))) continue;
+        real s0 = 0, s1 = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int i = 1; i < VS::Q; ++i) {
+            const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
+            int z1 = z + VS::c(i, 2);
+            if (p.z_mode == kZPeriodic) z1 = wrapn(z1, p.nz);
+            else if (z1 < 0 || z1 >= p.nz) continue;
+            if (solid_at(p, x1, y1, z1, 0) || solid_at(p, x1, y1, z1, 1)) continue;
+            const long long r1 = ridx(p, x1, y1, z1);
+            s0 += p.rho_cur[r1];
+            s1 += p.rho_cur[comp + r1];
+            ++cnt;
+        }
+        real m0, m1;
+        if (cnt > 0) { m0 = s0 / real(cnt); m1 = s1 / real(cnt); }
+        else { m0 = real(0); m1 = p.rho0[1]; }
+        const long long r = ridx(p, x, y, z);
+        p.rho_cur[r] = m0;
+        p.rho_cur[comp + r] = m1;
+        if (in_region(R, x, y, z, p.nx, p.ny)) { c0 += (double)m0; c1 += (double)m1; }
+    }
+    warp_add(p.acc + kAccCreated, c0);
+    warp_add(p.acc + kAccCreated + 1, c1);
+}
+
+// fictitious density of solid node (x, y, z) of step n (Eq. 18): the
+// zeta-scaled, w-weighted mean over its fluid neighbours
+template <class VS, typename real>
+__device__ __forceinline__ void wall_rho(const StepArgs<real>& p, int x, int y, int z, real* o0, real* o1) {
+    const long long comp = p.N + 2 * p.plane;
+    real n0 = 0, n1 = 0, den = 0;
+#pragma unroll
+    for (int i = 1; i < VS::Q; ++i) {
+        const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
+        int z1 = z + VS::c(i, 2);
+        if (p.z_mode == kZPeriodic) z1 = wrapn(z1, p.nz);
+        else if (z1 < 0 || z1 >= p.nz) continue;
+        if (solid_at(p, x1, y1, z1, 1)) continue;
+        const long long r1 = ridx(p, x1, y1, z1);
+        const real w = (real)VS::w(i);
+        n0 += w * p.rho_cur[r1];
+        n1 += w * p.rho_cur[comp + r1];
+        den += w;
+    }
+    *o0 = den > real(0) ? p.zeta[0] * n0 / den : real(0);
+    *o1 = den > real(0) ? p.zeta[1] * n1 / den : real(0);
+}
+
+// 3. wall densities on solid nodes of R1 and the ghost planes z = -1, z = nz
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g) {
+    const long long comp = p.N + 2 * p.plane;
+    const long long total = region_sites(R1g);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        region_site(R1g, t, p.nx, p.ny, &x, &y, &z);
+        real o0, o1;
+        if (z < 0 || z >= p.nz) {
+            if (p.z_mode != kZWalls) continue;
+            if (z >= p.nz && p.top_mode == kTopOpen) {
+                // open top: zero normal gradient, copy of the top plane
+                const int zt = p.nz - 1;
+                if (solid_at(p, x, y, zt, 1)) {
+                    wall_rho<VS>(p, x, y, zt, &o0, &o1);
+                } else {
+                    const long long rt = ridx(p, x, y, zt);
+                    o0 = p.rho_cur[rt];
+                    o1 = p.rho_cur[comp + rt];
+                }
+            } else {
+                wall_rho<VS>(p, x, y, z, &o0, &o1);  // substrate or lid
+            }
+        } else {
+            if (!solid_at(p, x, y, z, 1)) continue;
+            wall_rho<VS>(p, x, y, z, &o0, &o1);
+        }
+        const long long r = ridx(p, x, y, z);
+        p.rho_cur[r] = o0;
+        p.rho_cur[comp + r] = o1;
+    }
+}
+
+// neighbour accessor over the density array of the step
+template <class VS, typename real>
+struct ArrayNb {
+    const StepArgs<real>* p;
+    int x, y, z;
+    __device__ __forceinline__ void operator()(int i, real* cY, real* cB, real* rn) const {
+        const long long comp = p->N + 2 * p->plane;
+        const int x1 = wrapn(x + VS::c(i, 0), p->nx), y1 = wrapn(y + VS::c(i, 1), p->ny);
+        int z1 = z + VS::c(i, 2);
+        if (p->z_mode == kZPeriodic) z1 = wrapn(z1, p->nz);
+        const long long r1 = ridx(*p, x1, y1, z1);
+        const real a = p->rho_cur[r1], b = p->rho_cur[comp + r1];
+        const real tot = a + b;
+        *cY = a / tot;
+        *cB = b / tot;
+        *rn = phase_field(*p, a, b);
+    }
+};
+
+template <typename real>
+__device__ __forceinline__ void store_fields(const StepArgs<real>& p, long long s, const SiteOut<real>& so,
+                                             real solid) {
+    real* F = p.fields;
+    F[kFRhoInk * p.N + s] = so.rhoY;
+    F[kFRhoAmb * p.N + s] = so.rhoB;
+    F[kFUx * p.N + s] = so.u[0];
+    F[kFUy * p.N + s] = so.u[1];
+    F[kFUz * p.N + s] = so.u[2];
+    F[kFNu * p.N + s] = so.tau > real(0) ? (so.tau - real(0.5)) * real(1.0 / 3.0) : real(0);
+    F[kFP * p.N + s] = p.pfac[0] * so.rhoY + p.pfac[1] * so.rhoB;
+    F[kFPhi * p.N + s] = so.rn;
+    F[kFSolid * p.N + s] = solid;
+}
+
+// 4. collision at every fluid node of step n in R
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_collide(StepArgs<real> p, Region R) {
+    const long long comp = p.N + 2 * p.plane;
+    double m0 = 0, m1 = 0, px = 0, py = 0, pz = 0;
+    int bad = 0;
+    const long long total = region_sites(R);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        region_site(R, t, p.nx, p.ny, &x, &y, &z);
+        const long long s = sidx(p, x, y, z);
+        if (solid_at(p, x, y, z, 1)) {
+            if (p.write_fields) {
+                SiteOut<real> so = {0, 0, {0, 0, 0}, 0, 0};
+                store_fields(p, s, so, real(1));
+            }
+            continue;
+        }
+        real f[2][VS::Q];
+        if (solid_at(p, x, y, z, 0)) {
+            // created node: equilibrium at the nozzle velocity (Sec. II B)
+            const long long r = ridx(p, x, y, z);
+            const real r0 = p.rho_cur[r], r1 = p.rho_cur[comp + r];
+            const real uu = p.vn[0] * p.vn[0] + p.vn[1] * p.vn[1] + p.vn[2] * p.vn[2];
+#pragma unroll
+            for (int i = 0; i < VS::Q; ++i) {
+                f[0][i] = feq_i<VS>(p.phi[0][i], i, r0, p.vn[0], p.vn[1], p.vn[2], uu);
+                f[1][i] = feq_i<VS>(p.phi[1][i], i, r1, p.vn[0], p.vn[1], p.vn[2], uu);
+            }
+        } else {
+            real bc[2] = {real(0), real(0)};
+            pull_general<VS>(p, x, y, z, f, bc);
+        }
+        ArrayNb<VS, real> nb{&p, x, y, z};
+        SiteOut<real> so;
+        const real zd = p.z_mode == kZWalls ? real(z) + real(0.5) : real(-1);
+        collide<VS>(p, f, nb, zd, &so);
+#pragma unroll
+        for (int i = 0; i < VS::Q; ++i) {
+            p.fout[(long long)i * p.N + s] = f[0][i];
+            p.fout[(long long)(VS::Q + i) * p.N + s] = f[1][i];
+        }
+        if (z >= p.nz - 2)
+            for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
+        if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
+        if (p.write_fields) {
+            store_fields(p, s, so, real(0));
+            m0 += (double)so.rhoY;
+            m1 += (double)so.rhoB;
+            const double rr = (double)so.rhoY + (double)so.rhoB;
+            px += rr * (double)so.u[0];
+            py += rr * (double)so.u[1];
+            pz += rr * (double)so.u[2];
+        }
+    }
+    if (p.write_fields) {
+        warp_add(p.acc + kAccMass, m0);
+        warp_add(p.acc + kAccMass + 1, m1);
+        warp_add(p.acc + kAccMom, px);
+        warp_add(p.acc + kAccMom + 1, py);
+        warp_add(p.acc + kAccMom + 2, pz);
+    }
+    if (bad) atomicOr(p.flags, 1);
+}
+
+// initial equilibrium state
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged, int have_u) {
+    const long long comp = p.N + 2 * p.plane;
+    double m0 = 0, m1 = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < p.N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % p.nx);
+        const int y = (int)((s / p.nx) % p.ny);
+        const int z = (int)(s / p.plane);
+        const long long r = ridx(p, x, y, z);
+        SiteOut<real> so = {0, 0, {0, 0, 0}, 0, 0};
+        if (solid_at(p, x, y, z, 1)) {
+            p.rho_cur[r] = real(0);
+            p.rho_cur[comp + r] = real(0);
+            store_fields(p, s, so, real(1));
+            continue;
+        }
+        real rY, rB, u[3] = {0, 0, 0};
+        if (staged) {
+            rY = p.fields[kFRhoInk * p.N + s];
+            rB = p.fields[kFRhoAmb * p.N + s];
+            if (have_u) {
+                u[0] = p.fields[kFUx * p.N + s];
+                u[1] = p.fields[kFUy * p.N + s];
+                u[2] = p.fields[kFUz * p.N + s];
+            }
+        } else {
+            const bool ink = p.nozzle && z >= p.gap && axis_d2(p, x, y, 1) < p.rin2;
+            rY = ink ? p.rho0[0] : real(0);
+            rB = ink ? real(0) : p.rho0[1];
+        }
+        const real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int i = 0; i < VS::Q; ++i) {
+            p.fout[(long long)i * p.N + s] = feq_i<VS>(p.phi[0][i], i, rY, u[0], u[1], u[2], uu);
+            p.fout[(long long)(VS::Q + i) * p.N + s] = feq_i<VS>(p.phi[1][i], i, rB, u[0], u[1], u[2], uu);
+        }
+        p.rho_cur[r] = rY;
+        p.rho_cur[comp + r] = rB;
+        if (z >= p.nz - 2)
+            for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = u[a];
+        so.rhoY = rY;
+        so.rhoB = rB;
+        so.u[0] = u[0]; so.u[1] = u[1]; so.u[2] = u[2];
+        so.tau = real(0);
+        so.rn = phase_field(p, rY, rB);
+        store_fields(p, s, so, real(0));
+        m0 += (double)rY;
+        m1 += (double)rB;
+    }
+    warp_add(p.acc + kAccMass, m0);
+    warp_add(p.acc + kAccMass + 1, m1);
+}
+
+}  // namespace
+
+template <class VS, typename real>
+int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st) {
+    if (region_sites(R) == 0) return 0;
+    k_stream_density<VS, real><<<blocks_for(region_sites(R2)), kThreads, 0, st>>>(p, R2, R);
+    k_created<VS, real><<<blocks_for(region_sites(R1)), kThreads, 0, st>>>(p, R1, R);
+    Region R1g = R1;
+    if (p.z_mode == kZWalls) {
+        if (R1g.z0 <= 0) R1g.z0 = -1;
+        if (R1g.z1 >= p.nz) R1g.z1 = p.nz + 1;
+    }
+    k_wall<VS, real><<<blocks_for(region_sites(R1g)), kThreads, 0, st>>>(p, R1g);
+    k_collide<VS, real><<<blocks_for(region_sites(R)), kThreads, 0, st>>>(p, R);
+    return 4;
+}
+
+template <class VS, typename real>
+int launch_init(const StepArgs<real>& p, int staged, int have_u, cudaStream_t st) {
+    k_init<VS, real><<<blocks_for(p.N), kThreads, 0, st>>>(p, staged, have_u);
+    return 1;
+}
+
+template int launch_plain<D3Q19, float>(const StepArgs<float>&, const Region&, const Region&, const Region&, cudaStream_t);
+template int launch_plain<D3Q19, double>(const StepArgs<double>&, const Region&, const Region&, const Region&, cudaStream_t);
+template int launch_plain<D2Q9, float>(const StepArgs<float>&, const Region&, const Region&, const Region&, cudaStream_t);
+template int launch_plain<D2Q9, double>(const StepArgs<double>&, const Region&, const Region&, const Region&, cudaStream_t);
+template int launch_init<D3Q19, float>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_init<D3Q19, double>(const StepArgs<double>&, int, int, cudaStream_t);
+template int launch_init<D2Q9, float>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_init<D2Q9, double>(const StepArgs<double>&, int, int, cudaStream_t);
+
+}  // namespace cglbm

@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs, field by field.
+
+Error measure: for each macroscopic field, max |gpu - oracle| / max |oracle|
+(the field's own scale). Bars: FP64 storage 1e-12, FP32 storage 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_02655_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho_ink", "rho_amb", "ux", "uy", "uz", "nu", "p", "rhoN")
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def _lbm():
+    from paper_2102_02655_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def field_errors(fg, fo, names=FIELDS):
+    out = {}
+    for k in names:
+        ref = np.asarray(fo[k], dtype=np.float64)
+        scale = np.abs(ref).max()
+        d = np.abs(np.asarray(fg[k], dtype=np.float64) - ref).max()
+        out[k] = d / scale if scale > 0 else d
+    return out
+
+
+def assert_close(fg, fo, tol, names=FIELDS, label=""):
+    errs = field_errors(fg, fo, names)
+    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    assert not bad, "%s: fields over %.1e: %s" % (label, tol, {k: "%.3e" % v for k, v in bad.items()})
+    # solid flags are integers: bit-exact
+    if "solid" in fo and "solid" in fg:
+        assert np.array_equal(np.asarray(fg["solid"]) != 0, np.asarray(fo["solid"]) != 0)
+    return errs
+
+
+def run_pair(shape, wl, steps, path, storage=None, init=None, seed=1):
+    lbm = _lbm()
+    params = dict(wl["params"])
+    if storage:
+        params["storage"] = storage
+    ref = O.Oracle(shape, params=params, geom=wl["geom"], rheo=wl["rheo"])
+    lat = lbm.Lattice(shape, params, wl["geom"], wl["rheo"], path=path)
+    if init is None and wl["geom"].get("nozzle", 1):
+        rY, rB = I.nozzle_fill(shape, wl["geom"])
+        rB = I.perturbed_ambient(shape, rB, seed=seed)
+        init = (rY, rB)
+    if init is not None:
+        ref.set_fields(*init)
+        lat.set_fields(*init)
+    ref.step(steps)
+    lat.step(steps)
+    fg = lat.fields()
+    fo = ref.fields()
+    lat.close()
+    return fg, fo, ref
+
+
+# ---------------------------------------------------------------------------
+# the small print run (64x32x32, FP64, 500 steps) on both paths
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_print_oracle():
+    wl = I.workload("small_print_f64")
+    shape = wl["shape"]
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rB = I.perturbed_ambient(shape, rB, seed=0)
+    ref = O.Oracle(shape, params=wl["params"], geom=wl["geom"], rheo=wl["rheo"])
+    ref.set_fields(rY, rB)
+    snaps = {}
+    done = 0
+    for n in (100, 500):
+        ref.step(n - done)
+        done = n
+        snaps[n] = (ref.fields(), ref.diag())
+    return wl, (rY, rB), snaps
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_small_print_f64_500_steps(small_print_oracle, path):
+    lbm = _lbm()
+    wl, init, snaps = small_print_oracle
+    lat = lbm.Lattice(wl["shape"], wl["params"], wl["geom"], wl["rheo"], path=path)
+    lat.set_fields(*init)
+    done = 0
+    for n in (100, 500):
+        lat.step(n - done)
+        done = n
+        fg = lat.fields()
+        fo, do = snaps[n]
+        assert_close(fg, fo, TOL["f64"], label="%s step %d" % (path, n))
+        for k in ("mass", "bc_flux", "created", "destroyed"):
+            assert np.allclose(fg["diag"][k], do[k], rtol=1e-11, atol=1e-11), k
+    lat.close()
+
+
+def test_small_print_f32(small_print_oracle):
+    lbm = _lbm()
+    wl, init, snaps = small_print_oracle
+    params = dict(wl["params"], storage="f32")
+    lat = lbm.Lattice(wl["shape"], params, wl["geom"], wl["rheo"], path="fused")
+    lat.set_fields(*init)
+    lat.step(100)
+    assert_close(lat.fields(), snaps[100][0], TOL["f32"], label="f32 fused step 100")
+    lat.step(400)
+    assert_close(lat.fields(), snaps[500][0], TOL["f32"], label="f32 fused step 500")
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# ragged sizes, several tiles, other boundary modes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("shape", [(37, 19, 23), (70, 13, 41)])
+def test_ragged_print_f64(shape, path):
+    nx, ny, nz = shape
+    wl = I.print_run(shape, 3.0, 6, 0.03, 0.04, 0.5, "f64", head_pos=(nx / 3.0 + 0.3, ny / 2.0 - 0.2))
+    fg, fo, _ = run_pair(shape, wl, 40, path)
+    assert_close(fg, fo, TOL["f64"], label="ragged %s %s" % (shape, path))
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_ragged_print_f32(path):
+    shape = (45, 26, 30)
+    wl = I.print_run(shape, 4.0, 8, 0.02, 0.03, 0.6, "f32", head_pos=(15.0, 13.0))
+    fg, fo, _ = run_pair(shape, wl, 60, path, storage="f32")
+    assert_close(fg, fo, TOL["f32"], label="ragged f32 %s" % path)
+
+
+def test_cross_law_and_drag_f64():
+    shape = (33, 20, 26)
+    wl = I.print_run(shape, 4.0, 8, 0.02, 0.03, 0.6, "f64", head_pos=(10.0, 10.0))
+    wl["rheo"] = dict(law=O.CROSS, nu0=0.4, nu_inf=0.02, lam=50.0, n=0.7, tau_min=0.51, tau_max=2.0)
+    wl["params"] = dict(wl["params"], drag_gamma=0.05, A=0.02)
+    fg, fo, _ = run_pair(shape, wl, 50, "fused")
+    assert_close(fg, fo, TOL["f64"], label="cross+drag")
+
+
+def test_periodic_droplet_f64_and_f32():
+    shape = (20, 17, 15)
+    rY, rB = I.droplet(shape, (9.5, 8.0, 7.2), 4.0, width=1.5)
+    wl = dict(params=dict(velset=1, storage="f64", A=0.02, beta=0.7, tau_amb=0.9),
+              geom=dict(nozzle=0, z_mode=O.Z_PERIODIC),
+              rheo=dict(law=O.POWER_LAW, n=0.6, K=0.05, tau_min=0.51, tau_max=2.0))
+    fg, fo, _ = run_pair(shape, wl, 60, "auto", init=(rY, rB))
+    assert_close(fg, fo, TOL["f64"], label="periodic f64")
+    fg, fo, _ = run_pair(shape, wl, 60, "auto", storage="f32", init=(rY, rB))
+    assert_close(fg, fo, TOL["f32"], label="periodic f32")
+
+
+def test_d2q9_droplet_paper_lattice():
+    shape = (48, 1, 40)
+    rY, rB = I.droplet(shape, (23.5, 0.0, 19.5), 9.0, width=1.5)
+    wl = dict(params=dict(velset=O.D2Q9, storage="f64", A=0.01, beta=0.7, tau_amb=1.0),
+              geom=dict(nozzle=0, z_mode=O.Z_PERIODIC),
+              rheo=dict(law=O.NEWTONIAN, nu0=1 / 6, tau_min=0.501, tau_max=5.0))
+    fg, fo, _ = run_pair(shape, wl, 200, "auto", init=(rY, rB))
+    assert_close(fg, fo, TOL["f64"], names=("rho_ink", "rho_amb", "ux", "uz", "nu", "p", "rhoN"), label="d2q9")
+
+
+def test_d2q9_print_channel():
+    shape = (60, 1, 30)
+    wl = I.print_run(shape, 5.0, 8, 0.02, 0.03, 0.6, "f64", head_pos=(20.0, 0.0))
+    wl["params"] = dict(wl["params"], velset=O.D2Q9)
+    fg, fo, _ = run_pair(shape, wl, 80, "auto")
+    assert_close(fg, fo, TOL["f64"], names=("rho_ink", "rho_amb", "ux", "uz", "nu", "p", "rhoN"), label="d2q9 print")
+
+
+def test_lid_and_body_force():
+    shape = (6, 5, 12)
+    wl = dict(params=dict(velset=1, storage="f64", body_force=(1e-5, 0.0, 0.0), tau_amb=0.8),
+              geom=dict(nozzle=0, z_mode=O.Z_WALLS, top_mode=O.TOP_WALL, top_vel=(0.01, 0.002, 0.0)),
+              rheo=dict(law=O.NEWTONIAN, nu0=0.1, tau_min=0.501, tau_max=5.0))
+    rY = np.zeros((12, 5, 6))
+    rY[3:8] = 0.4
+    rB = 1.0 - rY
+    fg, fo, _ = run_pair(shape, wl, 120, "auto", init=(rY, rB))
+    assert_close(fg, fo, TOL["f64"], label="lid")
+
+
+def test_tiny_lattices():
+    for shape in [(1, 1, 5), (2, 3, 4), (5, 3, 7)]:
+        nx, ny, nz = shape
+        rY = np.zeros((nz, ny, nx))
+        rY[nz // 2] = 0.5
+        wl = dict(params=dict(velset=1, storage="f64"),
+                  geom=dict(nozzle=0, z_mode=O.Z_WALLS, top_mode=O.TOP_OPEN, rho_top_amb=1.01),
+                  rheo=dict(law=O.POWER_LAW, n=0.6, K=0.05, tau_min=0.51, tau_max=2.0))
+        for path in ("plain", "fused"):
+            fg, fo, _ = run_pair(shape, wl, 25, path, init=(rY, 1.0 - rY))
+            assert_close(fg, fo, TOL["f64"], label="tiny %s %s" % (shape, path))
+
+
+# ---------------------------------------------------------------------------
+# invariants on the device
+# ---------------------------------------------------------------------------
+
+def test_gpu_mass_ledger_closes_f64():
+    lbm = _lbm()
+    shape = (48, 32, 40)
+    wl = I.print_run(shape, 5.0, 10, 0.05, 0.04, 0.6, "f64", head_pos=(14.0, 16.0))
+    lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path="fused")
+    m0 = np.array(lat.diag()["mass"])
+    lat.step(150)
+    d = lat.diag()
+    pred = m0 + np.array(d["bc_flux"]) + np.array(d["created"]) - np.array(d["destroyed"])
+    assert np.all(np.abs(np.array(d["mass"]) - pred) <= 1e-12 * m0.sum())
+    assert d["created"][1] > 0 and d["destroyed"][1] > 0 and d["bc_flux"][0] > 0
+    lat.close()
+
+
+def test_fused_equals_plain_f32():
+    lbm = _lbm()
+    shape = (64, 40, 48)
+    wl = I.print_run(shape, 6.0, 12, 0.02, 0.03, 0.6, "f32", head_pos=(20.0, 20.0))
+    outs = []
+    for path in ("plain", "fused"):
+        lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path=path)
+        lat.step(30)
+        outs.append(lat.fields())
+        lat.close()
+    errs = field_errors(outs[1], outs[0])
+    assert max(errs.values()) < 1e-6, errs
+
+
+def test_unstable_flag_from_host_injected_nan():
+    lbm = _lbm()
+    shape = (16, 8, 12)
+    wl = dict(params=dict(velset=1, storage="f32"),
+              geom=dict(nozzle=0, z_mode=O.Z_PERIODIC),
+              rheo=dict(law=O.NEWTONIAN, nu0=0.1, tau_min=0.51, tau_max=2.0))
+    lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"])
+    rY = np.zeros((12, 8, 16))
+    rB = np.ones((12, 8, 16))
+    rB[5, 3, 7] = np.nan
+    lat.set_fields(rY, rB)
+    lat.step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        lat.fields()
+    assert e.value.status == lbm.LBM_EUNSTABLE
+    lat.close()
+
+
+def test_state_errors():
+    lbm = _lbm()
+    lat = lbm.Lattice((8, 8, 8), dict(storage="f32"))
+    with pytest.raises(lbm.LBMError) as e:
+        lat.step(1)
+    assert e.value.status == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LBMError) as e:
+        lat.set_geometry(dict(nozzle=1, gap=0))
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LBMError) as e:
+        lat.set_rheology(dict(tau_min=0.5))
+    assert e.value.status == lbm.LBM_EINVAL
+    lat.set_geometry(dict(nozzle=0))
+    lat.set_rheology(dict())
+    lat.step(0)
+    lat.step(3)
+    assert lat.diag()["step"] == 3
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# the throughput workload at full size, in the launch configuration the
+# benchmark times (fused FP32)
+# ---------------------------------------------------------------------------
+
+def test_full_size_print_f32_against_oracle():
+    lbm = _lbm()
+    wl = I.workload("print_512x128x128")
+    shape = wl["shape"]
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rB = I.perturbed_ambient(shape, rB, seed=2)
+    lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path="fused")
+    lat.set_fields(rY, rB)
+    lat.step(3)
+    fg = lat.fields()
+    d = lat.diag()
+    lat.close()
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f64"), geom=wl["geom"], rheo=wl["rheo"])
+    ref.set_fields(rY, rB)
+    ref.step(3)
+    fo = ref.fields()
+    assert_close(fg, fo, TOL["f32"], label="512x128x128 f32 fused, 3 steps")
+    do = ref.diag()
+    assert np.allclose(d["mass"], do["mass"], rtol=1e-6)
