@@ -395,11 +395,18 @@ static void collide_site(const or_lattice* L, const double* fin, const double* n
         }
 
     /* recolouring (Eq. 14-16). Both lines use the zero-velocity equilibria
-     * sum_k rho_k phi^k_i (Eq. 15 prints u; reading: u = 0 as in Eq. 14). */
+     * sum_k rho_k phi^k_i (Eq. 15 prints u; reading: u = 0 as in Eq. 14).
+     * cos(phi_i) of Eq. 16 has no limit where grad rho^N vanishes inside a
+     * mixture (its direction is then rounding noise, yet the term keeps its
+     * full size). Reading: the denominator is sqrt(|grad rho^N|^2 + eps^2)
+     * with eps = 1e-4, which leaves interfaces (|grad| ~ 0.1-1) unchanged to
+     * 1e-7 and makes the term vanish smoothly with the gradient. */
+    const double geps = 1e-4;
+    const double gden = sqrt(gNn * gNn + geps * geps);
     for (int i = 0; i < Q; ++i) {
         double cosp = 0.0;
-        if (i != 0 && gNn > 0.0)
-            cosp = (L->c[i][0] * gN[0] + L->c[i][1] * gN[1] + L->c[i][2] * gN[2]) / (L->cnorm[i] * gNn);
+        if (i != 0)
+            cosp = (L->c[i][0] * gN[0] + L->c[i][1] * gN[1] + L->c[i][2] * gN[2]) / (L->cnorm[i] * gden);
         double e0 = rho_k[0] * L->phi[0][i] + rho_k[1] * L->phi[1][i];
         double g = L->p.beta * rho_k[0] * rho_k[1] / (rho * rho) * cosp * e0;
         out[i] = phY * fs[i] + g;
