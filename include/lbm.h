@@ -34,7 +34,7 @@ typedef enum {
     LBM_EINVAL = 1,     /* invalid argument or configuration */
     LBM_ENOMEM = 2,     /* device allocation failed */
     LBM_ECUDA = 3,      /* CUDA runtime error (sticky) */
-    LBM_EUNSTABLE = 4,  /* a site saw a negative density or a NaN */
+    LBM_EUNSTABLE = 4,  /* a site's total density was not finite and positive */
     LBM_ETIMEOUT = 5,   /* a bounded host wait ran out */
     LBM_ESTATE = 6      /* call out of order (e.g. lbm_step before geometry and rheology) */
 } lbm_status;
@@ -114,7 +114,7 @@ typedef struct {
     double created[2];     /* cumulative mass of nodes uncovered by the nozzle */
     double destroyed[2];   /* cumulative mass of nodes covered by the nozzle */
     long long step;        /* steps since lbm_set_geometry */
-    int unstable;          /* 1 if any site saw a negative density or a NaN */
+    int unstable;          /* 1 if any site's total density was not finite and positive */
 } lbm_diag;
 
 /* Field selection bits for lbm_fields; the buffers are taken in this order. */

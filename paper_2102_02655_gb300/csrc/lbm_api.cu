@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -124,6 +125,7 @@ void fill_model(const lbm_handle* h, StepArgs<real>& p) {
     p.zeta[1] = (real)c.zeta_amb;
     p.A = (real)c.A;
     p.beta = (real)c.beta;
+    p.rho_ref = (real)c.rho0_amb;
     p.nuB = (real)((c.tau_ambient - 0.5) / 3.0);
     for (int a = 0; a < 3; ++a) p.g[a] = (real)c.body_force[a];
     p.drag_gamma = (real)c.drag_gamma;
@@ -137,10 +139,11 @@ void fill_model(const lbm_handle* h, StepArgs<real>& p) {
             const double share = d3 ? D3Q19::phi_share(i) : D2Q9::phi_share(i);
             const double ph = i == 0 ? alpha[k] : (1.0 - alpha[k]) * share;
             p.phi[k][i] = (real)ph;
+            p.dphi[k][i] = (real)(ph - (d3 ? D3Q19::w(i) : D2Q9::w(i)));
             const int cx = d3 ? D3Q19::c(i, 0) : D2Q9::c(i, 0);
             pf += ph * cx * cx;
         }
-        for (int i = h->Q; i < kMaxQ; ++i) p.phi[k][i] = 0;
+        for (int i = h->Q; i < kMaxQ; ++i) p.phi[k][i] = p.dphi[k][i] = 0;
         p.pfac[k] = (real)pf;
     }
     const lbm_rheology& r = h->rheo;
@@ -408,7 +411,15 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->plane = (long long)cfg->nx * cfg->ny;
     h->N = h->plane * cfg->nz;
     h->esize = cfg->storage == LBM_F64 ? 8 : 4;
-    h->zchunk = cfg->nz >= 64 ? 32 : cfg->nz;
+    {
+        // z-planes per CTA of the fused kernel: enough CTAs for ~3 per SM,
+        // at least 4 planes so the two-plane prologue stays amortised
+        const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 7) / 8);
+        long long chunks = (152LL * 3 + tiles - 1) / tiles;
+        chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));
+        h->zchunk = std::max(4, (int)((cfg->nz + chunks - 1) / chunks));
+        if (const char* e = getenv("CGLBM_ZCHUNK")) h->zchunk = std::max(1, atoi(e));
+    }
 
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e != cudaSuccess) {
@@ -594,7 +605,7 @@ lbm_status lbm_fields(lbm_handle* h, unsigned mask, void* const* dst, int dst_on
         diag->step = h->step;
         diag->unstable = flag ? 1 : 0;
     }
-    if (flag) return fail(h, LBM_EUNSTABLE, "lbm_fields: a site saw a negative density or a NaN");
+    if (flag) return fail(h, LBM_EUNSTABLE, "lbm_fields: a site's total density was not finite and positive");
     return LBM_OK;
 }
 

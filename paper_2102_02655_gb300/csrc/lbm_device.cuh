@@ -3,6 +3,13 @@
 // lattice constants, the nozzle template in fixed point, streaming with the
 // boundary rules, and the collision at one site. Shared by the phase-by-phase
 // kernels and the fused bulk kernel so that both compute the same arithmetic.
+//
+// Storage of a site: slot 0 holds the ink populations f^Y_i; slot 1 holds the
+// deviation of the total populations from rest, d_i = f^Y_i + f^B_i - w_i
+// rho_ref. Every step is linear in the populations, so streaming and the
+// boundary rules act on d directly; moments and stresses of the mixture come
+// from the small numbers d_i, and the ink mass in the ambient stays exact
+// (its populations are tiny there). This keeps FP32 storage accurate.
 #pragma once
 
 #include <cstdint>
@@ -108,7 +115,9 @@ struct StepArgs {
     real rho_top;      // imposed ambient density at the open top
     real rho0[2], zeta[2], A, beta, nuB, g[3], drag_gamma, drag_height;
     real phi[2][kMaxQ];
+    real dphi[2][kMaxQ];  // phi^k_i - w_i (zero at density ratio one)
     real pfac[2];      // p^k = pfac[k] rho^k (Eq. 9)
+    real rho_ref;      // reference total density of the stored deviation
     int law, max_iter;
     real nu0, nu_inf, lambda, n_exp, K, tau_min, tau_max, tol;
     // state
@@ -174,17 +183,6 @@ __device__ __forceinline__ bool solid_at(const StepArgs<real>& p, int x, int y, 
     if (!p.nozzle || z < p.gap) return false;
     long long d2 = axis_d2(p, x, y, which);
     return d2 >= p.rin2 && d2 <= p.rout2;
-}
-
-// ---------------------------------------------------------------------------
-// Equilibrium (Eq. 6, with 2 c_s^4 under (c.u)^2)
-// ---------------------------------------------------------------------------
-
-template <class VS, typename real>
-__device__ __forceinline__ real feq_i(real phi_i, int i, real rho, real ux, real uy, real uz, real uu) {
-    const real cu = (real)VS::c(i, 0) * ux + (real)VS::c(i, 1) * uy + (real)VS::c(i, 2) * uz;
-    const real w = (real)VS::w(i);
-    return rho * (phi_i + w * (real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu));
 }
 
 // ---------------------------------------------------------------------------
@@ -288,28 +286,47 @@ __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int
             f[1][i] = p.fin[(long long)(VS::Q + i) * p.N + src];
             continue;
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const real own = p.fin[(long long)(k * VS::Q + ib) * p.N + s];
-            real v;
-            if (kind == kLinkRest) {
-                v = own;
-            } else if (kind == kLinkMoving) {
-                const real rw = wall_density<VS>(p, k, x, y, z, i, s);
-                const real ucb = -((real)VS::c(i, 0) * uw[0] + (real)VS::c(i, 1) * uw[1] + (real)VS::c(i, 2) * uw[2]);
-                v = own - real(2) * (real)VS::w(ib) * rw * ucb * real(3);
-            } else {
-                real u2[3];
-                anti_bb_velocity<VS>(p, x, y, z, i, u2);
-                const real rw = k == 0 ? real(0) : p.rho_top;
-                const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
-                const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
-                v = -own + real(2) * rw * (p.phi[k][ib] + (real)VS::w(ib) * (real(4.5) * cu * cu - real(1.5) * uu));
-            }
-            f[k][i] = v;
-            bc[k] += v - own;
+        const real oY = p.fin[(long long)ib * p.N + s];            // f*^Y_ib(x), heading to the boundary
+        const real oD = p.fin[(long long)(VS::Q + ib) * p.N + s];  // d*_ib(x)
+        const real w = (real)VS::w(ib);
+        real vY, vD;
+        if (kind == kLinkRest) {
+            vY = oY;
+            vD = oD;
+        } else if (kind == kLinkMoving) {
+            // Eq. 26 per component; for the total the wall densities add up
+            const real rwY = wall_density<VS>(p, 0, x, y, z, i, s);
+            const real rwB = wall_density<VS>(p, 1, x, y, z, i, s);
+            const real ucb = -((real)VS::c(i, 0) * uw[0] + (real)VS::c(i, 1) * uw[1] + (real)VS::c(i, 2) * uw[2]);
+            vY = oY - real(6) * w * rwY * ucb;
+            vD = oD - real(6) * w * (rwY + rwB) * ucb;
+        } else {
+            // Eq. 28 with imposed densities 0 (ink) and rho_top (ambient)
+            real u2[3];
+            anti_bb_velocity<VS>(p, x, y, z, i, u2);
+            const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
+            const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+            const real q = real(4.5) * cu * cu - real(1.5) * uu;
+            vY = -oY;
+            vD = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
         }
+        f[0][i] = vY;
+        f[1][i] = vD;
+        bc[0] += vY - oY;
+        bc[1] += (vD - oD) - (vY - oY);
     }
+}
+
+// ink population and total deviation of the equilibrium pair at density
+// (rY, rB) and velocity u (Eq. 6): f^Y_i and sum_k f^k,eq_i - w_i rho_ref
+template <class VS, typename real>
+__device__ __forceinline__ void feq_pair(const StepArgs<real>& p, int i, real rY, real rB, real ux, real uy, real uz,
+                                         real uu, real* eY, real* eD) {
+    const real cu = (real)VS::c(i, 0) * ux + (real)VS::c(i, 1) * uy + (real)VS::c(i, 2) * uz;
+    const real w = (real)VS::w(i);
+    const real base = real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu;
+    *eY = rY * (p.phi[0][i] + w * base);
+    *eD = rY * p.dphi[0][i] + rB * p.dphi[1][i] + w * ((rY + rB) - p.rho_ref) + (rY + rB) * w * base;
 }
 
 // ---------------------------------------------------------------------------
@@ -412,18 +429,20 @@ template <class VS, typename real, typename Nb>
 __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q], const Nb& nb, real zdist,
                                         SiteOut<real>* so) {
     constexpr int Q = VS::Q;
-    // moments (Eq. 2-3)
-    real rY = 0, rB = 0, mx = 0, my = 0, mz = 0;
+    // moments (Eq. 2-3): ink density from slot 0, total density and momentum
+    // from the deviation slot (sum_i w_i c_i = 0)
+    real rY = 0, sd = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         rY += f[0][i];
-        rB += f[1][i];
-        const real ft = f[0][i] + f[1][i];
-        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? ft : -ft;
-        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? ft : -ft;
-        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? ft : -ft;
+        sd += f[1][i];
+        const real d = f[1][i];
+        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? d : -d;
+        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? d : -d;
+        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? d : -d;
     }
-    const real rho = rY + rB;
+    const real rho = p.rho_ref + sd;
+    const real rB = rho - rY;
     const real irho = real(1) / rho;
     const real ux = mx * irho, uy = my * irho, uz = mz * irho;
     const real uu = ux * ux + uy * uy + uz * uz;
@@ -452,40 +471,73 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
         F[a] = cB0 * gY[a] - cY0 * gB[a];
     }
     const real Fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
-    const real gNn = rsqrt_(gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2]);
+    const real gN2 = gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2];
+    const real gNn = rsqrt_(gN2);
 
-    // non-equilibrium stress of each component (Eq. 20):
-    // Pi^neq = sum_i f c c - rho_k (pfac_k I + u u)
-    real P[2][6];  // xx yy zz xy xz yz
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        real sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+    // non-equilibrium stresses (Eq. 20): ink Pi^Y = sum f^Y c c - rY (pfac_Y I + u u),
+    // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
+    real PY[6], PT[6];  // xx yy zz xy xz yz
+    {
+        real a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+        real b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0, b5 = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const real v = f[k][i];
+            const real v = f[0][i], d = f[1][i];
             const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-            if (cx) sxx += v;
-            if (cy) syy += v;
-            if (cz) szz += v;
-            if (cx && cy) sxy += (cx == cy) ? v : -v;
-            if (cx && cz) sxz += (cx == cz) ? v : -v;
-            if (cy && cz) syz += (cy == cz) ? v : -v;
+            if (cx) { a0 += v; b0 += d; }
+            if (cy) { a1 += v; b1 += d; }
+            if (cz) { a2 += v; b2 += d; }
+            if (cx && cy) { a3 += (cx == cy) ? v : -v; b3 += (cx == cy) ? d : -d; }
+            if (cx && cz) { a4 += (cx == cz) ? v : -v; b4 += (cx == cz) ? d : -d; }
+            if (cy && cz) { a5 += (cy == cz) ? v : -v; b5 += (cy == cz) ? d : -d; }
         }
-        const real rk = k == 0 ? rY : rB;
-        const real pk = p.pfac[k] * rk;
-        P[k][0] = sxx - (pk + rk * ux * ux);
-        P[k][1] = syy - (pk + rk * uy * uy);
-        P[k][2] = szz - (pk + rk * uz * uz);
-        P[k][3] = sxy - rk * ux * uy;
-        P[k][4] = sxz - rk * ux * uz;
-        P[k][5] = syz - rk * uy * uz;
-        if (VS::kPlanar) { P[k][1] = 0; P[k][3] = 0; P[k][5] = 0; }
+        const real pY = p.pfac[0] * rY;
+        const real pT = rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0)) +
+                        (rho - p.rho_ref) * real(1.0 / 3.0);
+        PT[0] = b0 - (pT + rho * ux * ux);
+        PT[1] = b1 - (pT + rho * uy * uy);
+        PT[2] = b2 - (pT + rho * uz * uz);
+        PT[3] = b3 - rho * ux * uy;
+        PT[4] = b4 - rho * ux * uz;
+        PT[5] = b5 - rho * uy * uz;
+        PY[0] = a0 - (pY + rY * ux * ux);
+        PY[1] = a1 - (pY + rY * uy * uy);
+        PY[2] = a2 - (pY + rY * uz * uz);
+        PY[3] = a3 - rY * ux * uy;
+        PY[4] = a4 - rY * ux * uz;
+        PY[5] = a5 - rY * uy * uz;
+        if (sizeof(real) < sizeof(double) && rY > real(1e-3) * rho) {
+            // FP32 storage: where the ink carries the rheology, sum its stress
+            // in double (the populations convert exactly), so that only the
+            // storage rounding of f^Y remains, not the cancellation in the sums
+            double c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, rYd = (double)f[0][0];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const double v = (double)f[0][i];
+                const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+                rYd += v;
+                if (cx) c0 += v;
+                if (cy) c1 += v;
+                if (cz) c2 += v;
+                if (cx && cy) c3 += (cx == cy) ? v : -v;
+                if (cx && cz) c4 += (cx == cz) ? v : -v;
+                if (cy && cz) c5 += (cy == cz) ? v : -v;
+            }
+            const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
+            PY[0] = (real)(c0 - (pYd + rYd * uxd * uxd));
+            PY[1] = (real)(c1 - (pYd + rYd * uyd * uyd));
+            PY[2] = (real)(c2 - (pYd + rYd * uzd * uzd));
+            PY[3] = (real)(c3 - rYd * uxd * uyd);
+            PY[4] = (real)(c4 - rYd * uxd * uzd);
+            PY[5] = (real)(c5 - rYd * uyd * uzd);
+        }
+        if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
     }
 
     // local relaxation time: ink viscosity from Eq. 24-25, harmonic mixing
     // by mass fraction (Eq. 17), clamp
-    const real S = rsqrt_(P[0][0] * P[0][0] + P[0][1] * P[0][1] + P[0][2] * P[0][2] +
-                          real(2) * (P[0][3] * P[0][3] + P[0][4] * P[0][4] + P[0][5] * P[0][5]));
+    const real S = rsqrt_(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
+                          real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
     const real tauY = solve_tau_ink(p, S, rY, rho);
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
     const real inv_nu = cY0 / nuY + cB0 / p.nuB;
@@ -503,44 +555,45 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     const real vx = ux + Fb[0] * irho, vy = uy + Fb[1] * irho, vz = uz + Fb[2] * irho;
     const real vv = vx * vx + vy * vy + vz * vz;
 
-    // perturbation (Eq. 10) once on the total, recolouring (Eq. 14-16)
+    // perturbation (Eq. 10) once on the total; recolouring (Eq. 14-16) with
+    // cos(phi_i) regularised as c.grad / (|c| sqrt(|grad|^2 + eps^2)), eps = 1e-4
     const bool pert = gNn > real(0) && Fn2 > real(0);
     const real pA = pert ? real(0.5) * p.A * gNn : real(0);
     const real iFn2 = pert ? real(1) / Fn2 : real(0);
-    const real rec = gNn > real(0) ? p.beta * rY * rB * irho * irho / gNn : real(0);
-    const real trY = P[0][0] + P[0][1] + P[0][2], trB = P[1][0] + P[1][1] + P[1][2];
+    const real rec = p.beta * rY * rB * irho * irho / rsqrt_(gN2 + real(1e-8));
+    const real trT = PT[0] + PT[1] + PT[2];
 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
         const real w = (real)VS::w(i);
         const real cu = cx * ux + cy * uy + cz * uz;
-        // regularised BGK: f^eq + (1 - 1/tau) w/(2 c_s^4) (c.Pi.c - c_s^2 tr Pi)
-        real qY = cx * cx * P[0][0] + cy * cy * P[0][1] + cz * cz * P[0][2] +
-                  real(2) * (cx * cy * P[0][3] + cx * cz * P[0][4] + cy * cz * P[0][5]) - trY * real(1.0 / 3.0);
-        real qB = cx * cx * P[1][0] + cy * cy * P[1][1] + cz * cz * P[1][2] +
-                  real(2) * (cx * cy * P[1][3] + cx * cz * P[1][4] + cy * cz * P[1][5]) - trB * real(1.0 / 3.0);
+        // regularised BGK of each component, summed: the post-collision
+        // total is sum_k f^k,eq + (1 - 1/tau) w/(2 c_s^4) (c.Pi.c - c_s^2 tr Pi)
+        // with Pi the mixture's non-equilibrium stress (Pi is linear in f)
+        const real qT = cx * cx * PT[0] + cy * cy * PT[1] + cz * cz * PT[2] +
+                        real(2) * (cx * cy * PT[3] + cx * cz * PT[4] + cy * cz * PT[5]) - trT * real(1.0 / 3.0);
         const real base = real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu;
-        real fY = rY * (p.phi[0][i] + w * base) + om * w * real(4.5) * qY;
-        real fB = rB * (p.phi[1][i] + w * base) + om * w * real(4.5) * qB;
+        real dT = rY * p.dphi[0][i] + rB * p.dphi[1][i] + w * (rho - p.rho_ref) + rho * w * base +
+                  om * w * real(4.5) * qT;
         if (forced) {
             const real cv = cx * vx + cy * vy + cz * vz;
             const real dbase = w * ((real(3) * cv + real(4.5) * cv * cv - real(1.5) * vv) - base);
-            fY += rY * dbase;
-            fB += rB * dbase;
+            dT += rho * dbase;
         }
-        real fs = fY + fB;
         if (pert) {
             const real Fc = cx * F[0] + cy * F[1] + cz * F[2];
-            fs += pA * (w * Fc * Fc * iFn2 - (real)VS::B(i));
+            dT += pA * (w * Fc * Fc * iFn2 - (real)VS::B(i));
         }
         real gcol = real(0);
         if (i != 0) {
             const real cg = (cx * gN[0] + cy * gN[1] + cz * gN[2]) * (real)VS::inv_norm(i);
             gcol = rec * cg * (rY * p.phi[0][i] + rB * p.phi[1][i]);
         }
-        f[0][i] = cY0 * fs + gcol;
-        f[1][i] = cB0 * fs - gcol;
+        // recolouring: ink share of the post-collision total plus the
+        // segregation term; the total (hence d) is unchanged
+        f[0][i] = cY0 * (w * p.rho_ref + dT) + gcol;
+        f[1][i] = dT;
     }
 
     so->rhoY = rY;
@@ -552,11 +605,12 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     so->rn = rn0;
 }
 
-// unstable: NaN, non-positive total density, or a clearly negative component
+// unstable: the total density is not finite and positive (a vanishing
+// component may dip slightly below zero at moving walls; that is not flagged)
 template <typename real>
 __device__ __forceinline__ bool unstable_site(real rY, real rB) {
     const real rho = rY + rB;
-    return !(rho > real(0)) || rY < real(-1e-3) * rho || rB < real(-1e-3) * rho;
+    return !(rho > real(0) && rho < real(1e6));
 }
 
 }  // namespace cglbm

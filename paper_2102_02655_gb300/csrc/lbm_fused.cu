@@ -36,13 +36,15 @@ __device__ __forceinline__ void pull_bulk(const StepArgs<real>& p, int x, int y,
             const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
             const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
             const real q = real(4.5) * cu * cu - real(1.5) * uu;
-            const real o0 = p.fin[(long long)ib * p.N + s];
-            const real o1 = p.fin[(long long)(19 + ib) * p.N + s];
-            f[0][i] = -o0;  // imposed ink density 0
-            f[1][i] = -o1 + real(2) * p.rho_top * (p.phi[1][ib] + (real)VS::w(ib) * q);
+            const real w = (real)VS::w(ib);
+            const real oY = p.fin[(long long)ib * p.N + s];
+            const real oD = p.fin[(long long)(19 + ib) * p.N + s];
+            // imposed densities: ink 0, ambient rho_top
+            f[0][i] = -oY;
+            f[1][i] = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
             if (kLedger) {
-                bc[0] += f[0][i] - o0;
-                bc[1] += f[1][i] - o1;
+                bc[0] += f[0][i] - oY;
+                bc[1] += (f[1][i] - oD) - (f[0][i] - oY);
             }
         } else {
             const int sx = wrap1(x - VS::c(i, 0), p.nx), sy = wrap1(y - VS::c(i, 1), p.ny);
@@ -62,7 +64,7 @@ __device__ __forceinline__ void pull_bulk_density(const StepArgs<real>& p, int x
 #pragma unroll
     for (int i = 0; i < 19; ++i) { a += f[0][i]; b += f[1][i]; }
     *rY = a;
-    *rB = b;
+    *rB = (p.rho_ref + b) - a;
 }
 
 __device__ __forceinline__ void warp_add(double* dst, double v) {

@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(kThreads) k_stream_density(StepArgs<real> p, R
         real f[2][VS::Q];
         real bc[2] = {real(0), real(0)};
         pull_general<VS>(p, x, y, z, f, bc);
-        real rY = 0, rB = 0;
+        real rY = 0, sd = 0;
 #pragma unroll
-        for (int i = 0; i < VS::Q; ++i) { rY += f[0][i]; rB += f[1][i]; }
+        for (int i = 0; i < VS::Q; ++i) { rY += f[0][i]; sd += f[1][i]; }
+        const real rB = (p.rho_ref + sd) - rY;
         const long long r = ridx(p, x, y, z);
         p.rho_cur[r] = rY;
         p.rho_cur[comp + r] = rB;
@@ -236,10 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_collide(StepArgs<real> p, Region R
             const real r0 = p.rho_cur[r], r1 = p.rho_cur[comp + r];
             const real uu = p.vn[0] * p.vn[0] + p.vn[1] * p.vn[1] + p.vn[2] * p.vn[2];
 #pragma unroll
-            for (int i = 0; i < VS::Q; ++i) {
-                f[0][i] = feq_i<VS>(p.phi[0][i], i, r0, p.vn[0], p.vn[1], p.vn[2], uu);
-                f[1][i] = feq_i<VS>(p.phi[1][i], i, r1, p.vn[0], p.vn[1], p.vn[2], uu);
-            }
+            for (int i = 0; i < VS::Q; ++i)
+                feq_pair<VS>(p, i, r0, r1, p.vn[0], p.vn[1], p.vn[2], uu, &f[0][i], &f[1][i]);
         } else {
             real bc[2] = {real(0), real(0)};
             pull_general<VS>(p, x, y, z, f, bc);
@@ -311,8 +310,10 @@ __global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged,
         const real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
         for (int i = 0; i < VS::Q; ++i) {
-            p.fout[(long long)i * p.N + s] = feq_i<VS>(p.phi[0][i], i, rY, u[0], u[1], u[2], uu);
-            p.fout[(long long)(VS::Q + i) * p.N + s] = feq_i<VS>(p.phi[1][i], i, rB, u[0], u[1], u[2], uu);
+            real eY, eD;
+            feq_pair<VS>(p, i, rY, rB, u[0], u[1], u[2], uu, &eY, &eD);
+            p.fout[(long long)i * p.N + s] = eY;
+            p.fout[(long long)(VS::Q + i) * p.N + s] = eD;
         }
         p.rho_cur[r] = rY;
         p.rho_cur[comp + r] = rB;

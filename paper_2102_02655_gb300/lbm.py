@@ -275,7 +275,10 @@ class Lattice:
         self.dtype = torch.float64 if st in ("f64", LBM_F64) else torch.float32
         self.device = torch.device("cuda", device)
         if stream is None:
-            stream = torch.cuda.current_stream(self.device)
+            # a stream of its own: handle 0 would mean "library-created stream"
+            # to the C ABI, and events recorded on torch's default stream would
+            # not order with it
+            stream = torch.cuda.Stream(self.device)
         self.stream = stream
         self._allocator = _TorchAllocator(self.device)
         cfg = make_config(self.shape, self.params, path=path, device=device, stream=stream.cuda_stream)
