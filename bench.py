@@ -174,7 +174,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     build.build()
-    wl = I.workload(WORKLOAD)
+    wl = I.workload(args.workload)
     shape = wl["shape"]
     nsites = shape[0] * shape[1] * shape[2]
     storage = wl["params"]["storage"]
@@ -236,6 +236,39 @@ def run_ours(args):
 
     # end to end through the C ABI with pinned host buffers: upload the
     # initial fields, K steps, read back densities, velocity and diagnostics
+    esz = 4 if storage == "f32" else 8
+    e2e, unstable = None, 0
+    if not args.no_e2e:
+        e2e, unstable = run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        cs = max(1, args.cpu_steps)
+        mlups, dt, n = oracle_mlups(args.workload, cs)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": O.threads_used(), "kind": "oracle",
+               "sample": "%s full lattice (%d sites), %d steps after 1 untimed, %.1f s" % (args.workload, n, cs, dt)}
+
+    lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+                "config": {"workload": args.workload, "lattice": "D3Q19", "sites": nsites,
+                           "path": "fused bulk kernel + phase-by-phase nozzle box",
+                           "nozzle": "r 10, gap 20, head 0.01 l.u./step, power-law n 0.6, extrusion 0.02",
+                           "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * nsites * esz * 2 / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "unstable": unstable}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
+    import numpy as np
+    import torch
+    from paper_2102_02655_gb300 import lbm
     npd = np.float32 if storage == "f32" else np.float64
     tdt = torch.float32 if storage == "f32" else torch.float64
     h_rY = torch.from_numpy(rY.astype(npd)).pin_memory()
@@ -254,31 +287,7 @@ def run_ours(args):
            "h2d_bytes_per_step": 2 * nsites * esz / args.steps,
            "d2h_bytes_per_step": (5 * nsites * esz + 120) / args.steps,
            "what": "per request: pinned H2D of rho_ink, rho_amb; K steps; D2H of rho_ink, rho_amb, u, diag"}
-    unstable = res["diag"]["unstable"]
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle as O
-        cs = max(1, args.cpu_steps)
-        mlups, dt, n = oracle_mlups(WORKLOAD, cs)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": O.threads_used(), "kind": "oracle",
-               "sample": "%s full lattice (%d sites), %d steps after 1 untimed, %.1f s" % (WORKLOAD, n, cs, dt)}
-
-    lat.close()
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
-                "config": {"workload": WORKLOAD, "lattice": "D3Q19", "sites": nsites,
-                           "path": "fused bulk kernel + phase-by-phase nozzle box",
-                           "nozzle": "r 10, gap 20, head 0.01 l.u./step, power-law n 0.6, extrusion 0.02",
-                           "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * nsites * esz * 2 / 1e9),
-                           "parallelism": "replicas" if ws > 1 else "single"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "unstable": unstable}
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return e2e, res["diag"]["unstable"]
 
 
 def main():
@@ -289,6 +298,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="throughput workload (default: the 512x128x128 print lattice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -46,6 +46,10 @@ struct lbm_handle {
     bool dead = false;  // sticky CUDA error
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the nozzle-box kernels run on a second stream, concurrently with the
+    // bulk kernel (disjoint writes, shared read-only input), joined per step
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     int Q = 19;
     long long N = 0, plane = 0;
     size_t esize = 8;  // bytes per real
@@ -109,6 +113,7 @@ void dev_free(lbm_handle* h, void* p) {
 
 bool is_fused(const lbm_handle* h) {
     if (h->cfg.velset != LBM_D3Q19) return false;
+    if (38.0 * (double)h->N >= 2147483647.0) return false;  // the fused kernel indexes in 32 bits
     if (h->geom.z_mode != LBM_Z_WALLS || h->geom.top_mode != LBM_TOP_OPEN) return false;
     return h->cfg.path != LBM_PATH_PLAIN;
 }
@@ -133,6 +138,7 @@ void fill_model(const lbm_handle* h, StepArgs<real>& p) {
     const bool d3 = c.velset == LBM_D3Q19;
     const double w0 = d3 ? 1.0 / 3.0 : 4.0 / 9.0;
     const double alpha[2] = {c.alpha_ink > 0 ? c.alpha_ink : w0, c.alpha_amb > 0 ? c.alpha_amb : w0};
+    p.unit = (c.rho0_ink == c.rho0_amb && alpha[0] == w0 && alpha[1] == w0) ? 1 : 0;
     for (int k = 0; k < 2; ++k) {
         double pf = 0.0;
         for (int i = 0; i < h->Q; ++i) {
@@ -268,8 +274,8 @@ lbm_status fold_events(lbm_handle* h) {
     return LBM_OK;
 }
 
-// record the begin (end = false) or end event of a timed group
-lbm_status mark(lbm_handle* h, int g, bool end, long long sites) {
+// record the begin (end = false) or end event of a timed group on stream st
+lbm_status mark(lbm_handle* h, int g, bool end, long long sites, cudaStream_t st) {
     if (!h->profiling) return LBM_OK;
     if (!end && h->nev[g] == lbm_handle::kMaxEv) {
         lbm_status st = fold_events(h);
@@ -281,7 +287,7 @@ lbm_status mark(lbm_handle* h, int g, bool end, long long sites) {
             cudaError_t e = cudaEventCreate(&h->ev[g][k][b]);
             if (e != cudaSuccess) return cuda_check(h, e, "cudaEventCreate");
         }
-    cudaError_t e = cudaEventRecord(h->ev[g][k][end ? 1 : 0], h->stream);
+    cudaError_t e = cudaEventRecord(h->ev[g][k][end ? 1 : 0], st);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaEventRecord");
     if (end) {
         h->ev_sites[g][k] = sites;
@@ -312,19 +318,27 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
             p.box = box;
             const long long box_sites = (long long)box.wx * box.wy * (box.z1 - box.z0);
             if (box.wx > 0) {
-                if ((st = mark(h, 1, false, 0)) != LBM_OK) return st;
+                cudaError_t e = cudaEventRecord(h->fork, h->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "fork");
+                if ((st = mark(h, 1, false, 0, h->side)) != LBM_OK) return st;
                 launched += launch_plain<VS, real>(p, box, grow(box, 1, nx, ny, nz), grow(box, 2, nx, ny, nz),
-                                                   h->stream);
-                if ((st = mark(h, 1, true, box_sites)) != LBM_OK) return st;
+                                                   h->side);
+                if ((st = mark(h, 1, true, box_sites, h->side)) != LBM_OK) return st;
             }
-            if ((st = mark(h, 0, false, 0)) != LBM_OK) return st;
+            if ((st = mark(h, 0, false, 0, h->stream)) != LBM_OK) return st;
             launched += launch_fused<real>(p, h->zchunk, h->stream);
-            if ((st = mark(h, 0, true, h->N - box_sites)) != LBM_OK) return st;
+            if ((st = mark(h, 0, true, h->N - box_sites, h->stream)) != LBM_OK) return st;
+            if (box.wx > 0) {
+                cudaError_t e = cudaEventRecord(h->join, h->side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->join, 0);
+                if (e != cudaSuccess) return cuda_check(h, e, "join");
+            }
         } else {
             const Region R = full_region(h);
-            if ((st = mark(h, 1, false, 0)) != LBM_OK) return st;
+            if ((st = mark(h, 1, false, 0, h->stream)) != LBM_OK) return st;
             launched += launch_plain<VS, real>(p, R, R, R, h->stream);
-            if ((st = mark(h, 1, true, h->N)) != LBM_OK) return st;
+            if ((st = mark(h, 1, true, h->N, h->stream)) != LBM_OK) return st;
         }
         h->launches += launched;
         cudaError_t e = cudaGetLastError();
@@ -437,6 +451,14 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
             return LBM_ECUDA;
         }
         h->own_stream = true;
+    }
+    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        fail(nullptr, LBM_ECUDA, "lbm_create: side stream: %s", cudaGetErrorString(e));
+        lbm_destroy(h);
+        return LBM_ECUDA;
     }
     const size_t fbytes = (size_t)2 * h->Q * h->N * h->esize;
     const size_t rbytes = (size_t)2 * (h->N + 2 * h->plane) * h->esize;
@@ -625,6 +647,12 @@ void lbm_destroy(lbm_handle* h) {
         for (int k = 0; k < lbm_handle::kMaxEv; ++k)
             for (int b = 0; b < 2; ++b)
                 if (h->ev[g][k][b]) cudaEventDestroy(h->ev[g][k][b]);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

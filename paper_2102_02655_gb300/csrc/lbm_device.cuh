@@ -118,6 +118,7 @@ struct StepArgs {
     real dphi[2][kMaxQ];  // phi^k_i - w_i (zero at density ratio one)
     real pfac[2];      // p^k = pfac[k] rho^k (Eq. 9)
     real rho_ref;      // reference total density of the stored deviation
+    int unit;          // rho0_ink == rho0_amb and phi = w for both (density ratio one)
     int law, max_iter;
     real nu0, nu_inf, lambda, n_exp, K, tau_min, tau_max, tol;
     // state
@@ -425,50 +426,93 @@ __device__ __forceinline__ real phase_field(const StepArgs<real>& p, real rY, re
     return (aY - aB) / (aY + aB);
 }
 
-template <class VS, typename real, typename Nb>
+// Collision at one fluid site (Eq. 4-20, 29), written over the pairs of
+// opposite directions (2p-1, 2p): even moments take pair sums, odd moments
+// pair differences, and each pair's two outputs share their even part.
+//   f[0][i]: ink populations, f[1][i]: total deviation d_i (see the storage
+//   note at the top); both replaced by the post-collision values.
+//   kUnit: reference densities equal and phi = w (density ratio one); the
+//   neighbour accessor then returns the ink fraction cY only, since
+//   rho_B/rho = 1 - cY and rho^N = 2 cY - 1. Otherwise it returns
+//   (cY, cB, rho^N).
+//   zdist: distance to the substrate (drag zone), < 0 when there is none.
+template <class VS, typename real, bool kUnit, typename Nb>
 __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q], const Nb& nb, real zdist,
                                         SiteOut<real>* so) {
     constexpr int Q = VS::Q;
+    constexpr int NP = (Q - 1) / 2;
+    // pair sums and differences
+    real sY[NP], sD[NP], dD[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        sY[q] = f[0][2 * q + 1] + f[0][2 * q + 2];
+        sD[q] = f[1][2 * q + 1] + f[1][2 * q + 2];
+        dD[q] = f[1][2 * q + 1] - f[1][2 * q + 2];
+    }
     // moments (Eq. 2-3): ink density from slot 0, total density and momentum
     // from the deviation slot (sum_i w_i c_i = 0)
-    real rY = 0, sd = 0, mx = 0, my = 0, mz = 0;
+    real rY = f[0][0], sd = f[1][0], mx = 0, my = 0, mz = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        rY += f[0][i];
-        sd += f[1][i];
-        const real d = f[1][i];
-        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? d : -d;
-        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? d : -d;
-        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? d : -d;
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
+        rY += sY[q];
+        sd += sD[q];
+        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? dD[q] : -dD[q];
+        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? dD[q] : -dD[q];
+        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? dD[q] : -dD[q];
     }
     const real rho = p.rho_ref + sd;
     const real rB = rho - rY;
     const real irho = real(1) / rho;
     const real ux = mx * irho, uy = my * irho, uz = mz * irho;
     const real uu = ux * ux + uy * uy + uz * uz;
-    const real cY0 = rY / rho, cB0 = rB / rho;
-    const real rn0 = phase_field(p, rY, rB);
+    const real cY0 = rY * irho, cB0 = rB * irho;
 
     // colour-gradient force (Eq. 11) and grad rho^N by the isotropic stencil
-    // (Eq. 12) in central-difference form, exactly zero on uniform fields
-    real gY[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gN[3] = {0, 0, 0};
+    // (Eq. 12), as pair differences 3 sum_p w_p c_p [chi(x + c_p) - chi(x - c_p)]:
+    // equal to the printed form (sum_i w_i c_i = 0) and exactly zero on a
+    // uniform field
+    real F[3], gN[3], rn0;
+    if constexpr (kUnit) {
+        real g[3] = {0, 0, 0};
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        real cY, cB, rn;
-        nb(i, &cY, &cB, &rn);
-        const real w = (real)VS::w(i);
-        const real dY = w * (cY - cY0), dB = w * (cB - cB0), dN = w * (rn - rn0);
+        for (int q = 0; q < NP; ++q) {
+            const int i = 2 * q + 1;
+            const real dd = (real)VS::w(i) * (nb(i) - nb(i + 1));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (VS::c(i, a) > 0) g[a] += dd;
+                else if (VS::c(i, a) < 0) g[a] -= dd;
+            }
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (VS::c(i, a) > 0) { gY[a] += dY; gB[a] += dB; gN[a] += dN; }
-            else if (VS::c(i, a) < 0) { gY[a] -= dY; gB[a] -= dB; gN[a] -= dN; }
+            F[a] = real(3) * g[a];            // grad(rho_Y/rho); F = (cB0 + cY0) grad cY
+            gN[a] = real(6) * g[a];           // rho^N = 2 cY - 1
         }
-    }
-    real F[3];
+        rn0 = cY0 - cB0;
+    } else {
+        real gY[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gR[3] = {0, 0, 0};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        gY[a] *= real(3); gB[a] *= real(3); gN[a] *= real(3);
-        F[a] = cB0 * gY[a] - cY0 * gB[a];
+        for (int q = 0; q < NP; ++q) {
+            const int i = 2 * q + 1;
+            real aY, aB, aN, bY, bB, bN;
+            nb(i, &aY, &aB, &aN);
+            nb(i + 1, &bY, &bB, &bN);
+            const real w = (real)VS::w(i);
+            const real dY = w * (aY - bY), dB = w * (aB - bB), dN = w * (aN - bN);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (VS::c(i, a) > 0) { gY[a] += dY; gB[a] += dB; gR[a] += dN; }
+                else if (VS::c(i, a) < 0) { gY[a] -= dY; gB[a] -= dB; gR[a] -= dN; }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            F[a] = real(3) * (cB0 * gY[a] - cY0 * gB[a]);
+            gN[a] = real(3) * gR[a];
+        }
+        rn0 = phase_field(p, rY, rB);
     }
     const real Fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
     const real gN2 = gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2];
@@ -478,58 +522,59 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
     real PY[6], PT[6];  // xx yy zz xy xz yz
     {
-        real a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-        real b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0, b5 = 0;
+        real a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const real v = f[0][i], d = f[1][i];
+        for (int q = 0; q < NP; ++q) {
+            const int i = 2 * q + 1;
             const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-            if (cx) { a0 += v; b0 += d; }
-            if (cy) { a1 += v; b1 += d; }
-            if (cz) { a2 += v; b2 += d; }
-            if (cx && cy) { a3 += (cx == cy) ? v : -v; b3 += (cx == cy) ? d : -d; }
-            if (cx && cz) { a4 += (cx == cz) ? v : -v; b4 += (cx == cz) ? d : -d; }
-            if (cy && cz) { a5 += (cy == cz) ? v : -v; b5 += (cy == cz) ? d : -d; }
+            if (cx) { a[0] += sY[q]; b[0] += sD[q]; }
+            if (cy) { a[1] += sY[q]; b[1] += sD[q]; }
+            if (cz) { a[2] += sY[q]; b[2] += sD[q]; }
+            if (cx && cy) { a[3] += (cx == cy) ? sY[q] : -sY[q]; b[3] += (cx == cy) ? sD[q] : -sD[q]; }
+            if (cx && cz) { a[4] += (cx == cz) ? sY[q] : -sY[q]; b[4] += (cx == cz) ? sD[q] : -sD[q]; }
+            if (cy && cz) { a[5] += (cy == cz) ? sY[q] : -sY[q]; b[5] += (cy == cz) ? sD[q] : -sD[q]; }
         }
         const real pY = p.pfac[0] * rY;
-        const real pT = rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0)) +
-                        (rho - p.rho_ref) * real(1.0 / 3.0);
-        PT[0] = b0 - (pT + rho * ux * ux);
-        PT[1] = b1 - (pT + rho * uy * uy);
-        PT[2] = b2 - (pT + rho * uz * uz);
-        PT[3] = b3 - rho * ux * uy;
-        PT[4] = b4 - rho * ux * uz;
-        PT[5] = b5 - rho * uy * uz;
-        PY[0] = a0 - (pY + rY * ux * ux);
-        PY[1] = a1 - (pY + rY * uy * uy);
-        PY[2] = a2 - (pY + rY * uz * uz);
-        PY[3] = a3 - rY * ux * uy;
-        PY[4] = a4 - rY * ux * uz;
-        PY[5] = a5 - rY * uy * uz;
+        real pT = (rho - p.rho_ref) * real(1.0 / 3.0);
+        if constexpr (!kUnit) pT += rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0));
+        PT[0] = b[0] - (pT + rho * ux * ux);
+        PT[1] = b[1] - (pT + rho * uy * uy);
+        PT[2] = b[2] - (pT + rho * uz * uz);
+        PT[3] = b[3] - rho * ux * uy;
+        PT[4] = b[4] - rho * ux * uz;
+        PT[5] = b[5] - rho * uy * uz;
+        PY[0] = a[0] - (pY + rY * ux * ux);
+        PY[1] = a[1] - (pY + rY * uy * uy);
+        PY[2] = a[2] - (pY + rY * uz * uz);
+        PY[3] = a[3] - rY * ux * uy;
+        PY[4] = a[4] - rY * ux * uz;
+        PY[5] = a[5] - rY * uy * uz;
         if (sizeof(real) < sizeof(double) && rY > real(1e-3) * rho) {
             // FP32 storage: where the ink carries the rheology, sum its stress
             // in double (the populations convert exactly), so that only the
             // storage rounding of f^Y remains, not the cancellation in the sums
-            double c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, rYd = (double)f[0][0];
+            double c[6] = {0, 0, 0, 0, 0, 0};
+            double rYd = (double)f[0][0];
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const double v = (double)f[0][i];
+            for (int q = 0; q < NP; ++q) {
+                const int i = 2 * q + 1;
+                const double v = (double)f[0][i] + (double)f[0][i + 1];
                 const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
                 rYd += v;
-                if (cx) c0 += v;
-                if (cy) c1 += v;
-                if (cz) c2 += v;
-                if (cx && cy) c3 += (cx == cy) ? v : -v;
-                if (cx && cz) c4 += (cx == cz) ? v : -v;
-                if (cy && cz) c5 += (cy == cz) ? v : -v;
+                if (cx) c[0] += v;
+                if (cy) c[1] += v;
+                if (cz) c[2] += v;
+                if (cx && cy) c[3] += (cx == cy) ? v : -v;
+                if (cx && cz) c[4] += (cx == cz) ? v : -v;
+                if (cy && cz) c[5] += (cy == cz) ? v : -v;
             }
             const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
-            PY[0] = (real)(c0 - (pYd + rYd * uxd * uxd));
-            PY[1] = (real)(c1 - (pYd + rYd * uyd * uyd));
-            PY[2] = (real)(c2 - (pYd + rYd * uzd * uzd));
-            PY[3] = (real)(c3 - rYd * uxd * uyd);
-            PY[4] = (real)(c4 - rYd * uxd * uzd);
-            PY[5] = (real)(c5 - rYd * uyd * uzd);
+            PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
+            PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
+            PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
+            PY[3] = (real)(c[3] - rYd * uxd * uyd);
+            PY[4] = (real)(c[4] - rYd * uxd * uzd);
+            PY[5] = (real)(c[5] - rYd * uyd * uzd);
         }
         if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
     }
@@ -542,58 +587,62 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
     const real inv_nu = cY0 / nuY + cB0 / p.nuB;
     const real tau = clampr(real(0.5) + real(3) / inv_nu, p.tau_min, p.tau_max);
-    const real om = real(1) - real(1) / tau;
+    const real om45 = (real(1) - real(1) / tau) * real(4.5);
 
-    // body force and drag by the exact difference method (Eq. 29)
+    // body force and drag by the exact difference method (Eq. 29): the
+    // equilibrium is taken at v = u + F/rho, f^eq(u) + [f^eq(v) - f^eq(u)]
     real Fb[3] = {rho * p.g[0], rho * p.g[1], rho * p.g[2]};
     if (p.drag_gamma != real(0) && zdist >= real(0) && zdist < p.drag_height) {
         Fb[0] -= p.drag_gamma * rY * ux;
         Fb[1] -= p.drag_gamma * rY * uy;
         Fb[2] -= p.drag_gamma * rY * uz;
     }
-    const bool forced = (Fb[0] != real(0)) || (Fb[1] != real(0)) || (Fb[2] != real(0));
     const real vx = ux + Fb[0] * irho, vy = uy + Fb[1] * irho, vz = uz + Fb[2] * irho;
-    const real vv = vx * vx + vy * vy + vz * vz;
+    const real vv15 = real(1.5) * (vx * vx + vy * vy + vz * vz);
 
     // perturbation (Eq. 10) once on the total; recolouring (Eq. 14-16) with
     // cos(phi_i) regularised as c.grad / (|c| sqrt(|grad|^2 + eps^2)), eps = 1e-4
     const bool pert = gNn > real(0) && Fn2 > real(0);
     const real pA = pert ? real(0.5) * p.A * gNn : real(0);
-    const real iFn2 = pert ? real(1) / Fn2 : real(0);
+    const real pAF = pert ? pA / Fn2 : real(0);
     const real rec = p.beta * rY * rB * irho * irho / rsqrt_(gN2 + real(1e-8));
-    const real trT = PT[0] + PT[1] + PT[2];
+    const real tr3 = (PT[0] + PT[1] + PT[2]) * real(1.0 / 3.0);
+    const real drho = rho - p.rho_ref;
 
+    // rest direction
+    {
+        const real w = (real)VS::w(0);
+        real e = w * drho - rho * w * vv15 + om45 * w * (-tr3) - pA * (real)VS::B(0);
+        if constexpr (!kUnit) e += rY * p.dphi[0][0] + rB * p.dphi[1][0];
+        f[1][0] = e;
+        f[0][0] = cY0 * (w * p.rho_ref + e);
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int q = 0; q < NP; ++q) {
+        const int i = 2 * q + 1;
         const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
         const real w = (real)VS::w(i);
-        const real cu = cx * ux + cy * uy + cz * uz;
-        // regularised BGK of each component, summed: the post-collision
-        // total is sum_k f^k,eq + (1 - 1/tau) w/(2 c_s^4) (c.Pi.c - c_s^2 tr Pi)
-        // with Pi the mixture's non-equilibrium stress (Pi is linear in f)
+        const real cv = cx * vx + cy * vy + cz * vz;
+        // even part: rest-frame share, quadratic equilibrium terms,
+        // regularised non-equilibrium (1 - 1/tau) w/(2 c_s^4) (c.Pi.c - c_s^2 tr Pi)
+        // and the perturbation; odd part: the linear equilibrium term
         const real qT = cx * cx * PT[0] + cy * cy * PT[1] + cz * cz * PT[2] +
-                        real(2) * (cx * cy * PT[3] + cx * cz * PT[4] + cy * cz * PT[5]) - trT * real(1.0 / 3.0);
-        const real base = real(3) * cu + real(4.5) * cu * cu - real(1.5) * uu;
-        real dT = rY * p.dphi[0][i] + rB * p.dphi[1][i] + w * (rho - p.rho_ref) + rho * w * base +
-                  om * w * real(4.5) * qT;
-        if (forced) {
-            const real cv = cx * vx + cy * vy + cz * vz;
-            const real dbase = w * ((real(3) * cv + real(4.5) * cv * cv - real(1.5) * vv) - base);
-            dT += rho * dbase;
-        }
-        if (pert) {
-            const real Fc = cx * F[0] + cy * F[1] + cz * F[2];
-            dT += pA * (w * Fc * Fc * iFn2 - (real)VS::B(i));
-        }
-        real gcol = real(0);
-        if (i != 0) {
-            const real cg = (cx * gN[0] + cy * gN[1] + cz * gN[2]) * (real)VS::inv_norm(i);
-            gcol = rec * cg * (rY * p.phi[0][i] + rB * p.phi[1][i]);
-        }
-        // recolouring: ink share of the post-collision total plus the
-        // segregation term; the total (hence d) is unchanged
-        f[0][i] = cY0 * (w * p.rho_ref + dT) + gcol;
-        f[1][i] = dT;
+                        real(2) * (cx * cy * PT[3] + cx * cz * PT[4] + cy * cz * PT[5]) - tr3;
+        const real Fc = cx * F[0] + cy * F[1] + cz * F[2];
+        real e = w * drho + rho * w * (real(4.5) * cv * cv - vv15) + om45 * w * qT +
+                 (pert ? pAF * w * Fc * Fc - pA * (real)VS::B(i) : real(0));
+        if constexpr (!kUnit) e += rY * p.dphi[0][i] + rB * p.dphi[1][i];
+        const real o = real(3) * rho * w * cv;
+        const real cg = (cx * gN[0] + cy * gN[1] + cz * gN[2]) * (real)VS::inv_norm(i);
+        real e0;
+        if constexpr (kUnit) e0 = rho * w;
+        else e0 = rY * p.phi[0][i] + rB * p.phi[1][i];
+        const real G = rec * cg * e0;
+        const real dp = e + o, dm = e - o;
+        f[1][i] = dp;
+        f[1][i + 1] = dm;
+        f[0][i] = cY0 * (w * p.rho_ref + dp) + G;
+        f[0][i + 1] = cY0 * (w * p.rho_ref + dm) - G;
     }
 
     so->rhoY = rY;

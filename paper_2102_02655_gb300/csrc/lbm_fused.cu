@@ -2,69 +2,85 @@
 // relaxation time, regularised collision, perturbation and recolouring for
 // every site outside the nozzle box (D3Q19, substrate below, open top).
 //
-// Each CTA owns a TX x TY column tile and marches up a chunk of z-planes. The
-// colour gradient (Eq. 12) needs the densities of this step at the 18
-// neighbours, which other CTAs produce; the CTA therefore recomputes, for the
-// plane ahead, the post-streaming densities of its tile plus a one-site halo
-// from the populations in HBM (the re-reads hit L2), and keeps three planes
-// of colour fractions in shared memory. HBM traffic stays at one read and one
-// write of the populations per site update.
+// Each CTA owns a 32 x 8 column tile and marches up a chunk of z-planes. The
+// colour gradient (Eq. 12) needs this step's densities at the 18 neighbours,
+// which other CTAs produce, so for the plane ahead the CTA pulls:
+//   - the populations of its own sites, kept in shared memory until the
+//     collision of that plane (one iteration later), and their densities;
+//   - the densities of the one-site halo ring around the tile (these re-reads
+//     of neighbouring tiles' populations are served by L2);
+// and keeps three planes of colour fractions in shared memory. HBM traffic is
+// one read and one write of the populations per site update.
+//
+// Indices are 32-bit (the host selects this kernel only when 38 N < 2^31);
+// the periodic wrap in x and y is resolved once per site into the source
+// column and row of each direction.
 #include "lbm_launch.h"
 
 namespace cglbm {
 
 namespace {
 
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;  // tile + one-site halo
+constexpr int NRING = HS - NT;                         // 84 halo sites
+constexpr int SX = TX + 4, SY = TY + 4, SS = SX * SY;  // tile + two rings (substrate ghost)
+static_assert(SS - HS <= NT && NRING <= NT, "ring sites must fit one item per thread");
+
+__device__ __forceinline__ int slot_of(int z) { return (z + 3) % 3; }
+
 // streaming for a site away from the nozzle: every source is fluid except
 // across the substrate (resting half-way wall) and the open top
-// (anti-bounce-back, Eq. 28)
-template <typename real, bool kLedger>
-__device__ __forceinline__ void pull_bulk(const StepArgs<real>& p, int x, int y, int z, real f[2][19],
-                                          real bc[2]) {
+// (anti-bounce-back, Eq. 28, with the velocity extrapolated from the last two
+// planes of the previous step). ledger adds the boundary-link mass changes.
+template <typename real>
+__device__ __forceinline__ void pull_fast(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19],
+                                          double bc[2], bool ledger) {
     using VS = D3Q19;
-    const long long s = sidx(p, x, y, z);
+    const int nx = p.nx, ny = p.ny, pl = (int)p.plane, N = (int)p.N;
+    const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+    const int r0 = gy * nx;
+    const int rm = (gy == 0 ? ny - 1 : gy - 1) * nx, rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
+    const int zoff = zz * pl;
+    const int s = zoff + r0 + gx;
+    const real* fin = p.fin;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const int sz = z - VS::c(i, 2);
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        const int sz = zz - cz;
         const int ib = opp(i);
         if (sz < 0) {
-            f[0][i] = p.fin[(long long)ib * p.N + s];
-            f[1][i] = p.fin[(long long)(19 + ib) * p.N + s];
+            f[0][i] = fin[ib * N + s];
+            f[1][i] = fin[(19 + ib) * N + s];
         } else if (sz >= p.nz) {
-            real u2[3];
-            anti_bb_velocity<VS>(p, x, y, z, i, u2);
-            const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
-            const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
-            const real q = real(4.5) * cu * cu - real(1.5) * uu;
+            // u_w = 1.5 u(x) - 0.5 u(x + c_i): the velocity of the last two
+            // planes of the previous step ([component][plane nz-2, nz-1][site])
+            real uw[3];
+            const int x1 = cx > 0 ? xp : (cx < 0 ? xm : gx), y1 = cy > 0 ? rp : (cy < 0 ? rm : r0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const real u0 = p.u_prev[a * 2 * pl + pl + r0 + gx];
+                uw[a] = p.nz >= 2 ? real(1.5) * u0 - real(0.5) * p.u_prev[a * 2 * pl + y1 + x1] : u0;
+            }
+            const real cu = (real)VS::c(ib, 0) * uw[0] + (real)VS::c(ib, 1) * uw[1] + (real)VS::c(ib, 2) * uw[2];
+            const real q = real(4.5) * cu * cu - real(1.5) * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
             const real w = (real)VS::w(ib);
-            const real oY = p.fin[(long long)ib * p.N + s];
-            const real oD = p.fin[(long long)(19 + ib) * p.N + s];
-            // imposed densities: ink 0, ambient rho_top
-            f[0][i] = -oY;
+            const real oY = fin[ib * N + s];
+            const real oD = fin[(19 + ib) * N + s];
+            f[0][i] = -oY;  // imposed ink density 0
             f[1][i] = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
-            if (kLedger) {
-                bc[0] += f[0][i] - oY;
-                bc[1] += (f[1][i] - oD) - (f[0][i] - oY);
+            if (ledger) {
+                bc[0] += (double)(f[0][i] - oY);
+                bc[1] += (double)((f[1][i] - oD) - (f[0][i] - oY));
             }
         } else {
-            const int sx = wrap1(x - VS::c(i, 0), p.nx), sy = wrap1(y - VS::c(i, 1), p.ny);
-            const long long src = sidx(p, sx, sy, sz);
-            f[0][i] = p.fin[(long long)i * p.N + src];
-            f[1][i] = p.fin[(long long)(19 + i) * p.N + src];
+            const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
+            const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
+            const int src = zoff - cz * pl + sy + sx;
+            f[0][i] = fin[i * N + src];
+            f[1][i] = fin[(19 + i) * N + src];
         }
     }
-}
-
-template <typename real>
-__device__ __forceinline__ void pull_bulk_density(const StepArgs<real>& p, int x, int y, int z, real* rY, real* rB) {
-    real f[2][19];
-    real bc[2];
-    pull_bulk<real, false>(p, x, y, z, f, bc);
-    real a = 0, b = 0;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) { a += f[0][i]; b += f[1][i]; }
-    *rY = a;
-    *rB = (p.rho_ref + b) - a;
 }
 
 __device__ __forceinline__ void warp_add(double* dst, double v) {
@@ -84,27 +100,72 @@ __device__ __forceinline__ bool in_box(const StepArgs<real>& p, int x, int y, in
     return dx < b.wx && dy < b.wy;
 }
 
-template <typename real, int TX, int TY>
-struct SmemNb {
-    const real (*sm)[3][(TX + 2) * (TY + 2)];
-    int slot[3];  // slots of planes z-1, z, z+1
-    int hidx;     // halo-tile index of the site
-    __device__ __forceinline__ void operator()(int i, real* cY, real* cB, real* rn) const {
-        const int j = hidx + D3Q19::c(i, 0) + D3Q19::c(i, 1) * (TX + 2);
-        const int sl = slot[1 + D3Q19::c(i, 2)];
-        *cY = sm[sl][0][j];
-        *cB = sm[sl][1][j];
-        *rn = sm[sl][2][j];
+template <typename real, bool kUnit>
+struct Colour {
+    static constexpr int NV = kUnit ? 1 : 3;
+    real* col;  // [3 slots][NV][HS]
+    __device__ __forceinline__ void put(const StepArgs<real>& p, int slot, int j, real rY, real rB) const {
+        const real inv = real(1) / (rY + rB);
+        if constexpr (kUnit) {
+            col[slot * HS + j] = rY * inv;
+        } else {
+            col[(slot * 3 + 0) * HS + j] = rY * inv;
+            col[(slot * 3 + 1) * HS + j] = rB * inv;
+            col[(slot * 3 + 2) * HS + j] = phase_field(p, rY, rB);
+        }
+    }
+    __device__ __forceinline__ void copy(int dst, int src, int j) const {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) col[(dst * NV + v) * HS + j] = col[(src * NV + v) * HS + j];
     }
 };
 
-template <typename real, int TX, int TY, int MINB>
-__global__ void __launch_bounds__(TX * TY, MINB) k_fused(StepArgs<real> p, int zchunk) {
-    constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;
-    constexpr int SX = TX + 4, SY = TY + 4, SS = SX * SY;
-    constexpr int NT = TX * TY;
-    __shared__ real sm[3][3][HS];
-    __shared__ real sub[2][SS];
+template <typename real, bool kUnit>
+struct SmemNb;
+template <typename real>
+struct SmemNb<real, true> {
+    const real* col;
+    int slot[3], hidx;
+    __device__ __forceinline__ real operator()(int i) const {
+        return col[slot[1 + D3Q19::c(i, 2)] * HS + hidx + D3Q19::c(i, 0) + D3Q19::c(i, 1) * HX];
+    }
+};
+template <typename real>
+struct SmemNb<real, false> {
+    const real* col;
+    int slot[3], hidx;
+    __device__ __forceinline__ void operator()(int i, real* cY, real* cB, real* rn) const {
+        const int j = hidx + D3Q19::c(i, 0) + D3Q19::c(i, 1) * HX;
+        const int sl = slot[1 + D3Q19::c(i, 2)];
+        *cY = col[(sl * 3 + 0) * HS + j];
+        *cB = col[(sl * 3 + 1) * HS + j];
+        *rn = col[(sl * 3 + 2) * HS + j];
+    }
+};
+
+__device__ __forceinline__ void ring_coord(int r, int* hx, int* hy) {
+    if (r < HX) { *hx = r; *hy = 0; }
+    else if (r < 2 * HX) { *hx = r - HX; *hy = HY - 1; }
+    else if (r < 2 * HX + HY - 2) { *hx = 0; *hy = 1 + r - 2 * HX; }
+    else { *hx = HX - 1; *hy = 1 + r - 2 * HX - (HY - 2); }
+}
+
+template <typename real>
+__device__ __forceinline__ void density(const real f[2][19], const StepArgs<real>& p, real* rY, real* rB) {
+    real a = 0, b = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) { a += f[0][i]; b += f[1][i]; }
+    *rY = a;
+    *rB = (p.rho_ref + b) - a;
+}
+
+template <typename real, bool kUnit, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][38][NT]
+    Colour<real, kUnit> C{pops + 2 * 38 * NT};     // [3 slots][NV][HS]
+    real* sub = pops + 38 * NT;                    // buffer 1, reused by the substrate prologue: [2][SS]
+    // (buffer 1 is first written after the prologue's last read of sub)
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int za = blockIdx.z * zchunk;
@@ -112,89 +173,105 @@ __global__ void __launch_bounds__(TX * TY, MINB) k_fused(StepArgs<real> p, int z
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x = x0 + tx, y = y0 + ty;
     const bool in_xy = x < p.nx && y < p.ny;
+    const int gx = in_xy ? x : wrapn(x, p.nx), gy = in_xy ? y : wrapn(y, p.ny);
+    const int hidx = (ty + 1) * HX + (tx + 1);
+    double bc[2] = {0.0, 0.0};
 
-    auto put = [&](int slot, int j, real rY, real rB) {
-        const real tot = rY + rB;
-        sm[slot][0][j] = rY / tot;
-        sm[slot][1][j] = rB / tot;
-        sm[slot][2][j] = phase_field(p, rY, rB);
-    };
-    // densities after streaming of plane zz over the tile and its halo
-    auto load_plane = [&](int zz, int slot) {
-        if (zz >= p.nz) {  // open top: copy of the top plane
-            const int src = (zz - 1 + 3) % 3;
-            for (int j = tid; j < HS; j += NT) {
-                sm[slot][0][j] = sm[src][0][j];
-                sm[slot][1][j] = sm[src][1][j];
-                sm[slot][2][j] = sm[src][2][j];
+    // Densities after streaming on plane zz for the tile and its halo ring
+    // (items 0 and 1), and with outer > 0 also the second ring (item 2, the
+    // substrate prologue). Item 0 is the thread's own site: its populations go
+    // to buffer zz & 1 and its boundary-link mass is booked once, for this
+    // chunk's planes. One pull body serves every item.
+    auto load_plane = [&](int zz, bool keep, bool outer) {
+        const int nitems = outer ? 3 : 2;
+        for (int it = 0; it < nitems; ++it) {
+            int hx, hy;  // coordinates in the tile grown by two rings
+            if (it == 0) {
+                hx = tx + 2;
+                hy = ty + 2;
+            } else if (it == 1) {
+                if (tid >= NRING) continue;
+                ring_coord(tid, &hx, &hy);
+                hx += 1;
+                hy += 1;
+            } else {
+                if (tid >= SS - HS) continue;
+                // the 92 sites of the second ring
+                const int j = tid;
+                if (j < SX) { hx = j; hy = 0; }
+                else if (j < 2 * SX) { hx = j - SX; hy = SY - 1; }
+                else { const int k = j - 2 * SX; hy = 1 + (k >> 1); hx = (k & 1) ? SX - 1 : 0; }
             }
-            return;
-        }
-        for (int j = tid; j < HS; j += NT) {
-            const int hx = j % HX, hy = j / HX;
-            const int gx = wrapn(x0 - 1 + hx, p.nx), gy = wrapn(y0 - 1 + hy, p.ny);
+            const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
+            const bool own = it == 0;
+            real f[2][19];
+            pull_fast(p, px, py, zz, f, bc, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
+            if (own && keep && in_xy) {
+                real* b = pops + (zz & 1) * 38 * NT + tid;
+#pragma unroll
+                for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
+            }
             real rY, rB;
-            pull_bulk_density(p, gx, gy, zz, &rY, &rB);
-            put(slot, j, rY, rB);
+            density(f, p, &rY, &rB);
+            if (outer) {
+                sub[hy * SX + hx] = rY;
+                sub[SS + hy * SX + hx] = rB;
+            }
+            if (it < 2) C.put(p, slot_of(zz), (hy - 1) * HX + (hx - 1), rY, rB);
         }
     };
 
     // prologue: planes za - 1 and za
     if (za == 0) {
-        // plane 0 with two rings, then the substrate ghost plane z = -1 from
-        // the fictitious-density rule (Eq. 18) over its five fluid neighbours
-        for (int j = tid; j < SS; j += NT) {
-            const int sx = j % SX, sy = j / SX;
-            const int gx = wrapn(x0 - 2 + sx, p.nx), gy = wrapn(y0 - 2 + sy, p.ny);
-            real rY, rB;
-            pull_bulk_density(p, gx, gy, 0, &rY, &rB);
-            sub[0][j] = rY;
-            sub[1][j] = rB;
-        }
+        // plane 0 with two rings, for the substrate ghost plane z = -1 built by
+        // the fictitious-density rule (Eq. 18) from its five fluid neighbours
+        load_plane(0, true, true);
         __syncthreads();
         for (int j = tid; j < HS; j += NT) {
             const int hx = j % HX, hy = j / HX;
             const int c = (hy + 1) * SX + (hx + 1);
-            put(0, j, sub[0][c], sub[1][c]);  // plane 0 -> slot 0
             real n0 = 0, n1 = 0, den = 0;
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
                 if (D3Q19::c(i, 2) != 1) continue;
                 const real w = (real)D3Q19::w(i);
                 const int cc = c + D3Q19::c(i, 0) + D3Q19::c(i, 1) * SX;
-                n0 += w * sub[0][cc];
-                n1 += w * sub[1][cc];
+                n0 += w * sub[cc];
+                n1 += w * sub[SS + cc];
                 den += w;
             }
-            put(2, j, p.zeta[0] * n0 / den, p.zeta[1] * n1 / den);  // plane -1 -> slot 2
+            C.put(p, 2, j, p.zeta[0] * n0 / den, p.zeta[1] * n1 / den);  // plane -1
         }
     } else {
-        load_plane(za - 1, (za - 1) % 3);
-        load_plane(za, za % 3);
+        load_plane(za - 1, false, false);
+        load_plane(za, true, false);
     }
 
-    double bc0 = 0, bc1 = 0, m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
+    double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
     int bad = 0;
-    const int hidx = (ty + 1) * HX + (tx + 1);
-
     for (int z = za; z < zb; ++z) {
-        __syncthreads();  // plane z-2's slot is free, plane z's writes visible
-        load_plane(z + 1, (z + 1) % 3);
+        __syncthreads();  // plane z-2's colour slot and population buffer are free
+        if (z + 1 < p.nz) {
+            load_plane(z + 1, true, false);
+        } else {
+            // open top: zero normal gradient, the ghost plane copies the top plane
+            for (int j = tid; j < HS; j += NT) C.copy(slot_of(z + 1), slot_of(z), j);
+        }
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
             real f[2][19];
-            real bc[2] = {real(0), real(0)};
-            pull_bulk<real, true>(p, x, y, z, f, bc);
-            bc0 += (double)bc[0];
-            bc1 += (double)bc[1];
-            SmemNb<real, TX, TY> nb{sm, {(z + 2) % 3, z % 3, (z + 1) % 3}, hidx};
+            const real* b = pops + (z & 1) * 38 * NT + tid;
+#pragma unroll
+            for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
+            SmemNb<real, kUnit> nb{C.col, {slot_of(z - 1), slot_of(z), slot_of(z + 1)}, hidx};
             SiteOut<real> so;
-            collide<D3Q19>(p, f, nb, real(z) + real(0.5), &so);
-            const long long s = sidx(p, x, y, z);
+            collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
+            const int s = z * (int)p.plane + y * p.nx + x;
+            const int N = (int)p.N;
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                p.fout[(long long)i * p.N + s] = f[0][i];
-                p.fout[(long long)(19 + i) * p.N + s] = f[1][i];
+                p.fout[i * N + s] = f[0][i];
+                p.fout[(19 + i) * N + s] = f[1][i];
             }
             if (z >= p.nz - 2)
                 for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
@@ -219,8 +296,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) k_fused(StepArgs<real> p, int z
             }
         }
     }
-    warp_add(p.acc + kAccBc, bc0);
-    warp_add(p.acc + kAccBc + 1, bc1);
+    warp_add(p.acc + kAccBc, bc[0]);
+    warp_add(p.acc + kAccBc + 1, bc[1]);
     if (p.write_fields) {
         warp_add(p.acc + kAccMass, m0);
         warp_add(p.acc + kAccMass + 1, m1);
@@ -231,18 +308,33 @@ __global__ void __launch_bounds__(TX * TY, MINB) k_fused(StepArgs<real> p, int z
     if (bad) atomicOr(p.flags, 1);
 }
 
+template <typename real, bool kUnit>
+constexpr size_t fused_smem() {
+    return sizeof(real) * (2 * 38 * NT + 3 * Colour<real, kUnit>::NV * HS);
+}
+
+template <typename real, bool kUnit, int MINB>
+int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
+    constexpr size_t smem = fused_smem<real, kUnit>();
+    static unsigned configured = 0;  // one bit per device: the attribute is set once per context
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 32 && !(configured & (1u << dev))) {
+        cudaFuncSetAttribute(k_fused<real, kUnit, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured |= 1u << dev;
+    }
+    dim3 block(TX, TY);
+    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + zchunk - 1) / zchunk);
+    k_fused<real, kUnit, MINB><<<grid, block, smem, st>>>(p, zchunk);
+    return 1;
+}
+
 }  // namespace
 
 template <typename real>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr int TX = 32, TY = 8;
-    dim3 block(TX, TY);
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + zchunk - 1) / zchunk);
-    if (sizeof(real) == 4)
-        k_fused<real, TX, TY, 2><<<grid, block, 0, st>>>(p, zchunk);
-    else
-        k_fused<real, TX, TY, 1><<<grid, block, 0, st>>>(p, zchunk);
-    return 1;
+    constexpr int MINB = sizeof(real) == 4 ? 2 : 1;
+    return p.unit ? launch_one<real, true, MINB>(p, zchunk, st) : launch_one<real, false, MINB>(p, zchunk, st);
 }
 
 template int launch_fused<float>(const StepArgs<float>&, int, cudaStream_t);

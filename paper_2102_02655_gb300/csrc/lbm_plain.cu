@@ -177,7 +177,23 @@ __global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g)
     }
 }
 
-// neighbour accessor over the density array of the step
+// neighbour accessors over the density array of the step: the ink fraction
+// (density ratio one), or ink and ambient fractions and the phase field
+template <class VS, typename real>
+struct ArrayNbUnit {
+    const StepArgs<real>* p;
+    int x, y, z;
+    __device__ __forceinline__ real operator()(int i) const {
+        const long long comp = p->N + 2 * p->plane;
+        const int x1 = wrapn(x + VS::c(i, 0), p->nx), y1 = wrapn(y + VS::c(i, 1), p->ny);
+        int z1 = z + VS::c(i, 2);
+        if (p->z_mode == kZPeriodic) z1 = wrapn(z1, p->nz);
+        const long long r1 = ridx(*p, x1, y1, z1);
+        const real a = p->rho_cur[r1], b = p->rho_cur[comp + r1];
+        return a / (a + b);
+    }
+};
+
 template <class VS, typename real>
 struct ArrayNb {
     const StepArgs<real>* p;
@@ -243,10 +259,15 @@ __global__ void __launch_bounds__(kThreads) k_collide(StepArgs<real> p, Region R
             real bc[2] = {real(0), real(0)};
             pull_general<VS>(p, x, y, z, f, bc);
         }
-        ArrayNb<VS, real> nb{&p, x, y, z};
         SiteOut<real> so;
         const real zd = p.z_mode == kZWalls ? real(z) + real(0.5) : real(-1);
-        collide<VS>(p, f, nb, zd, &so);
+        if (p.unit) {
+            ArrayNbUnit<VS, real> nb{&p, x, y, z};
+            collide<VS, real, true>(p, f, nb, zd, &so);
+        } else {
+            ArrayNb<VS, real> nb{&p, x, y, z};
+            collide<VS, real, false>(p, f, nb, zd, &so);
+        }
 #pragma unroll
         for (int i = 0; i < VS::Q; ++i) {
             p.fout[(long long)i * p.N + s] = f[0][i];

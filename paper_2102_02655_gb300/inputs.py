@@ -61,6 +61,8 @@ def workload(name):
     print_512x128x128: 512x128x128 FP32 print run (8.4M sites), radius 10,
         gap 20, n = 0.6, extrusion 0.02, head 0.01 (the throughput workload).
     print_128x64x64: the 128x64x64 downscale of the same run.
+    print_256x128x128: half of the throughput lattice (4.2M sites), the size
+        used for detailed kernel profiles.
     """
     if name == "small_print_f64":
         return print_run((64, 32, 32), 4.0, 12, 0.01, 0.02, 0.6, "f64", head_pos=(16.0, 16.0))
@@ -68,6 +70,8 @@ def workload(name):
         return print_run((512, 128, 128), 10.0, 20, 0.01, 0.02, 0.6, "f32")
     if name == "print_128x64x64":
         return print_run((128, 64, 64), 10.0, 20, 0.01, 0.02, 0.6, "f32")
+    if name == "print_256x128x128":
+        return print_run((256, 128, 128), 10.0, 20, 0.01, 0.02, 0.6, "f32")
     raise KeyError(name)
 
 

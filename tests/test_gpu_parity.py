@@ -8,7 +8,8 @@ velocity, pressure, phase field). The local viscosity nu is evaluated from the
 non-equilibrium stress, a quantity 10^-2..10^-3 the size of the populations it
 is computed from, so it amplifies population differences: its FP32 bar is
 5e-5, and for the Cross law (unbounded slope at zero shear) the FP64 bar adds
-the bound of cross_nu_floor. FP32 errors grow with simulated time (velocity
+the bound of cross_nu_floor. The phase field rho^N = 2 rho_Y/rho - 1 (density
+ratio one) doubles the colour-fraction error: its bar is twice the density bar. FP32 errors grow with simulated time (velocity
 round-off integrates into interface displacement): FP32 runs are compared at a
 200-step horizon, and the drift to 500 steps is bounded separately."""
 import numpy as np
@@ -63,6 +64,9 @@ def assert_close(fg, fo, tol, names=FIELDS, label="", nu_tol=None):
         nu_tol = NU_TOL["f32"] if tol >= TOL["f32"] else tol
     if "nu" in errs and errs["nu"] <= nu_tol:
         errs["nu"] = 0.0
+    # rho^N = 2 rho_Y/rho - 1 at density ratio one: twice the colour-fraction error
+    if "rhoN" in errs and errs["rhoN"] <= 2 * tol:
+        errs["rhoN"] = 0.0
     bad = {k: v for k, v in errs.items() if not (v <= tol)}
     assert not bad, "%s: fields over %.1e: %s" % (label, tol, {k: "%.3e" % v for k, v in bad.items()})
     # solid flags are integers: bit-exact
@@ -291,8 +295,8 @@ def test_fused_equals_plain_f32():
         lat.step(30)
         outs.append(lat.fields())
         lat.close()
-    errs = field_errors(outs[1], outs[0])
-    assert max(errs.values()) < 1e-6, errs
+    # the two paths round differently (reciprocals, summation order): FP32 bars
+    assert_close(outs[1], outs[0], TOL["f32"], label="fused vs plain f32")
 
 
 def test_unstable_flag_from_host_injected_nan():
