@@ -193,6 +193,51 @@ lbm_status lbm_profile(struct lbm_handle* h, int enable);
 /* Wait for the stream and return the totals since profiling was turned on. */
 lbm_status lbm_timings(struct lbm_handle* h, lbm_timing* out);
 
+/* One time step on population buffers the caller owns, with no device
+ * allocation at all. This entry point has no counterpart in the paper: it is
+ * for callers that cannot call cudaMalloc, such as code running inside
+ * another framework's memory pool or a pre-sized arena that forbids new
+ * allocations, and real-time loops where an allocation could stall or fail.
+ * lbm_create allocates the lattice state; this call does not: every device
+ * buffer comes from the caller, and the work space lives in one fixed static
+ * device array of LBM_NOALLOC_SCRATCH_BYTES inside the library (held by every
+ * GPU that loads the library, until the process exits).
+ *
+ * It runs the phase-by-phase kernels of lbm_step over the whole lattice.
+ *  cfg, g, r  lattice constants, geometry and rheology as for lbm_create,
+ *             lbm_set_geometry and lbm_set_ink_rheology; cfg->device selects
+ *             the GPU, cfg->cuda_stream the stream (NULL = the legacy default
+ *             stream); cfg->path, alloc, free and alloc_ctx are ignored.
+ *  step       index n >= 1 of the step taken: the nozzle moves from its step
+ *             n-1 to its step n position.
+ *  f_in       device buffer of 2*Q*N values (double for LBM_F64, else float):
+ *             the post-collision populations of step n-1, value (k*Q + i)*N +
+ *             site with site = (z*ny + y)*nx + x; slot k = 0 holds the ink
+ *             populations f^Y_i, slot k = 1 holds f^Y_i + f^B_i - w_i rho0_amb.
+ *             At rest with phi = w: slot 0 = w_i rho_ink, slot 1 =
+ *             w_i (rho_ink + rho_amb - rho0_amb).
+ *  f_out      device buffer of the same size for step n; must not overlap f_in.
+ *  fields     optional device buffer of 9*N values: rho_ink, rho_amb, ux, uy,
+ *             uz, nu, p, rho^N, solid of step n (NULL: not written).
+ *  diag       optional host struct: mass and momentum of step n (only when
+ *             fields is given, else 0) and this step's boundary flux and
+ *             created/destroyed mass; filling it waits for the stream.
+ * The previous step's densities and top-plane velocities are rebuilt from
+ * f_in (collision conserves each component's mass), so the result equals
+ * lbm_step's up to rounding. The first call on a device looks up the static
+ * array's device address; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the
+ * call clears what must start at zero): calls that overlap on the GPU race,
+ * so issue them on one stream or wait between them. Returns LBM_EINVAL for
+ * invalid arguments or a lattice whose work space (four densities per site
+ * plus the top planes' velocities) exceeds the array, about 500k sites in
+ * FP64 and 1M in FP32, LBM_ECUDA on a CUDA error,
+ * LBM_EUNSTABLE (diag requested) if a site's total density was not finite
+ * and positive. */
+#define LBM_NOALLOC_SCRATCH_BYTES (16u << 20)
+lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry* g, const lbm_rheology* r, long long step,
+                            const void* f_in, void* f_out, void* fields, lbm_diag* diag);
+
 typedef struct lbm_handle lbm_handle;
 
 #ifdef __cplusplus

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <type_traits>
@@ -683,3 +684,143 @@ lbm_status lbm_timings(lbm_handle* h, lbm_timing* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_step_noalloc: the work space of the step in a static device array
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
+
+// In host code g_noalloc_scratch names a host-side stand-in, not device
+// memory: the kernels get the address that the runtime reports for the
+// current device, looked up once per device.
+lbm_status noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 64) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = (unsigned char*)g_noalloc_addr[dev];
+    return LBM_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <class VS, typename real>
+lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void* f_out, void* fields, lbm_diag* diag,
+                        unsigned char* scratch, cudaStream_t st) {
+    StepArgs<real> p;
+    memset(&p, 0, sizeof(p));
+    fill_model(tmp, p);
+    fill_geometry(tmp, p, step);
+    const size_t es = sizeof(real);
+    const size_t rbytes = round256(2 * (size_t)(tmp->N + 2 * tmp->plane) * es);
+    const size_t ubytes = round256(6 * (size_t)tmp->plane * es);
+    double* acc = (double*)scratch;
+    int* flags = (int*)(scratch + 256);
+    real* rho_prev = (real*)(scratch + 512);
+    real* rho_cur = (real*)(scratch + 512 + rbytes);
+    real* u_prev = (real*)(scratch + 512 + 2 * rbytes);
+    real* u_cur = (real*)(scratch + 512 + 2 * rbytes + ubytes);
+    // the accumulators and the flag must start at zero; the density and
+    // velocity arrays are written before they are read
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 512, st);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaMemsetAsync: %s", cudaGetErrorString(e));
+    p.fin = (const real*)f_in;
+    p.fout = (real*)f_out;
+    p.rho_prev = rho_prev;
+    p.rho_cur = rho_cur;
+    p.u_prev = u_prev;
+    p.u_cur = u_cur;
+    p.fields = (real*)fields;
+    p.acc = acc;
+    p.flags = flags;
+    p.write_fields = fields ? 1 : 0;
+    p.box = Region{0, 0, 0, 0, 0, 0};
+    launch_prev_from_f<VS, real>(p, rho_prev, u_prev, st);
+    const Region R = full_region(tmp);
+    launch_plain<VS, real>(p, R, R, R, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: launch: %s", cudaGetErrorString(e));
+    if (!diag) return LBM_OK;
+    double a[kAccN];
+    int flag = 0;
+    e = cudaMemcpyAsync(a, acc, sizeof(a), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: diag: %s", cudaGetErrorString(e));
+    for (int k = 0; k < 2; ++k) {
+        diag->mass[k] = a[kAccMass + k];
+        diag->bc_flux[k] = a[kAccBc + k];
+        diag->created[k] = a[kAccCreated + k];
+        diag->destroyed[k] = a[kAccDestroyed + k];
+    }
+    for (int c = 0; c < 3; ++c) diag->momentum[c] = a[kAccMom + c];
+    diag->step = step;
+    diag->unstable = flag ? 1 : 0;
+    if (flag) return fail(nullptr, LBM_EUNSTABLE, "lbm_step_noalloc: a site's total density was not finite and positive");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry* g, const lbm_rheology* r,
+                                       long long step, const void* f_in, void* f_out, void* fields, lbm_diag* diag) {
+    if (!cfg || !g || !r) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: cfg, g and r are required");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || (cfg->velset != LBM_D2Q9 && cfg->velset != LBM_D3Q19) ||
+        (cfg->velset == LBM_D2Q9 && cfg->ny != 1) || (cfg->storage != LBM_F64 && cfg->storage != LBM_F32))
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid lattice sizes, velocity set or storage");
+    if (!(cfg->tau_ambient > 0.5) || !(cfg->rho0_ink > 0) || !(cfg->rho0_amb > 0) || cfg->alpha_ink >= 1.0 ||
+        cfg->alpha_amb >= 1.0 || !(cfg->beta >= 0.0 && cfg->beta <= 1.0))
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid model constants");
+    if (!(r->tau_min > 0.5) || !(r->tau_max >= r->tau_min) || r->law < LBM_NEWTONIAN || r->law > LBM_POWER_LAW)
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid rheology");
+    if ((g->z_mode != LBM_Z_PERIODIC && g->z_mode != LBM_Z_WALLS) || (g->top_mode != LBM_TOP_OPEN && g->top_mode != LBM_TOP_WALL) ||
+        (g->nozzle && (g->z_mode != LBM_Z_WALLS || g->gap < 1 || g->gap >= cfg->nz || !(g->r_inner > 0) ||
+                       !(g->wall_thickness > 0))))
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid geometry");
+    if (step < 1) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: step must be >= 1");
+    if (!f_in || !f_out) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: f_in and f_out are required");
+    const int Q = cfg->velset == LBM_D3Q19 ? 19 : 9;
+    const size_t es = cfg->storage == LBM_F64 ? 8 : 4;
+    const long long plane = (long long)cfg->nx * cfg->ny, N = plane * cfg->nz;
+    const size_t fbytes = (size_t)2 * Q * N * es;
+    const char* a = (const char*)f_in;
+    const char* b = (const char*)f_out;
+    if (a < b + fbytes && b < a + fbytes) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: f_in and f_out overlap");
+    const size_t need = 512 + 2 * round256(2 * (size_t)(N + 2 * plane) * es) + 2 * round256(6 * (size_t)plane * es);
+    if (need > (size_t)LBM_NOALLOC_SCRATCH_BYTES)
+        return fail(nullptr, LBM_EINVAL,
+                    "lbm_step_noalloc: the lattice needs %zu bytes of work space, the static array holds %u", need,
+                    (unsigned)LBM_NOALLOC_SCRATCH_BYTES);
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaSetDevice: %s", cudaGetErrorString(e));
+    unsigned char* scratch = nullptr;
+    lbm_status st = noalloc_scratch(cfg->device, &scratch);
+    if (st != LBM_OK) return st;
+    // the constants come from the same host code as lbm_step's, through a
+    // handle object on the stack that owns no device memory
+    lbm_handle tmp;
+    tmp.cfg = *cfg;
+    tmp.geom = *g;
+    tmp.rheo = *r;
+    tmp.Q = Q;
+    tmp.plane = plane;
+    tmp.N = N;
+    tmp.esize = es;
+    cudaStream_t stream = (cudaStream_t)cfg->cuda_stream;
+    if (cfg->velset == LBM_D3Q19)
+        return cfg->storage == LBM_F64 ? noalloc_step<D3Q19, double>(&tmp, step, f_in, f_out, fields, diag, scratch, stream)
+                                       : noalloc_step<D3Q19, float>(&tmp, step, f_in, f_out, fields, diag, scratch, stream);
+    return cfg->storage == LBM_F64 ? noalloc_step<D2Q9, double>(&tmp, step, f_in, f_out, fields, diag, scratch, stream)
+                                   : noalloc_step<D2Q9, float>(&tmp, step, f_in, f_out, fields, diag, scratch, stream);
+}

@@ -27,4 +27,11 @@ int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st);
 template <class VS, typename real>
 int launch_init(const StepArgs<real>& p, int staged, int have_u, cudaStream_t st);
 
+// Rebuild the previous step's densities (every fluid node of the step-(n-1)
+// geometry) and the physical velocity of the last two planes from the
+// post-collision populations p.fin: collision conserves each component's
+// mass, and its momentum is rho u + F (exact difference method).
+template <class VS, typename real>
+int launch_prev_from_f(const StepArgs<real>& p, real* rho_prev, real* u_prev, cudaStream_t st);
+
 }  // namespace cglbm

@@ -353,7 +353,54 @@ __global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged,
     warp_add(p.acc + kAccMass + 1, m1);
 }
 
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_prev_from_f(StepArgs<real> p, real* rho_prev, real* u_prev) {
+    const long long comp = p.N + 2 * p.plane;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < p.N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % p.nx);
+        const int y = (int)((s / p.nx) % p.ny);
+        const int z = (int)(s / p.plane);
+        if (solid_at(p, x, y, z, 0)) continue;
+        real rY = 0, sd = 0, m[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < VS::Q; ++i) {
+            const real a = p.fin[(long long)i * p.N + s], d = p.fin[(long long)(VS::Q + i) * p.N + s];
+            rY += a;
+            sd += d;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (VS::c(i, c)) m[c] += VS::c(i, c) > 0 ? d : -d;
+        }
+        const real rho = p.rho_ref + sd;
+        const long long r = ridx(p, x, y, z);
+        rho_prev[r] = rY;
+        rho_prev[comp + r] = rho - rY;
+        if (z >= p.nz - 2) {
+            // m = rho u + F with F = rho g - gamma rho_Y u in the drag zone
+            const bool zone = p.z_mode == kZWalls && p.drag_gamma != real(0) && real(z) + real(0.5) < p.drag_height;
+            const real den = zone ? rho - p.drag_gamma * rY : rho;
+            for (int a = 0; a < 3; ++a) {
+                const real ub = (m[a] - rho * p.g[a]) / den;
+                const real F = rho * p.g[a] - (zone ? p.drag_gamma * rY * ub : real(0));
+                u_prev[utop_idx(p, a, x, y, z)] = ub + real(0.5) * F / rho;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+template <class VS, typename real>
+int launch_prev_from_f(const StepArgs<real>& p, real* rho_prev, real* u_prev, cudaStream_t st) {
+    k_prev_from_f<VS, real><<<blocks_for(p.N), kThreads, 0, st>>>(p, rho_prev, u_prev);
+    return 1;
+}
+
+template int launch_prev_from_f<D3Q19, float>(const StepArgs<float>&, float*, float*, cudaStream_t);
+template int launch_prev_from_f<D3Q19, double>(const StepArgs<double>&, double*, double*, cudaStream_t);
+template int launch_prev_from_f<D2Q9, float>(const StepArgs<float>&, float*, float*, cudaStream_t);
+template int launch_prev_from_f<D2Q9, double>(const StepArgs<double>&, double*, double*, cudaStream_t);
 
 template <class VS, typename real>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st) {

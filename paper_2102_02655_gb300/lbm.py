@@ -34,7 +34,7 @@ ALL_FIELDS = 0x7F
 
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
            "lbm_fields", "lbm_sync", "lbm_destroy", "lbm_last_error", "lbm_kernel_launches",
-           "lbm_profile", "lbm_timings")
+           "lbm_profile", "lbm_timings", "lbm_step_noalloc")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -102,8 +102,10 @@ def lib():
         L.lbm_kernel_launches.restype = C.c_longlong
         L.lbm_profile.argtypes = [H, C.c_int]
         L.lbm_timings.argtypes = [H, C.POINTER(lbm_timing)]
+        L.lbm_step_noalloc.argtypes = [C.POINTER(lbm_config), C.POINTER(lbm_geometry), C.POINTER(lbm_rheology),
+                                       C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbm_diag)]
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
-                     "lbm_fields", "lbm_sync", "lbm_profile", "lbm_timings"):
+                     "lbm_fields", "lbm_sync", "lbm_profile", "lbm_timings", "lbm_step_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -169,6 +171,13 @@ def lbm_last_error(h):
 
 def lbm_kernel_launches(h):
     return lib().lbm_kernel_launches(h)
+
+
+def lbm_step_noalloc(cfg, geom, rheo, step, f_in_ptr, f_out_ptr, fields_ptr=None, diag=None):
+    """One step on caller-owned device buffers without any device allocation
+    (see include/lbm.h). Returns the status; raises nothing."""
+    return lib().lbm_step_noalloc(C.byref(cfg), C.byref(geom), C.byref(rheo), int(step), f_in_ptr, f_out_ptr,
+                                  fields_ptr, C.byref(diag) if diag is not None else None)
 
 
 def lbm_profile(h, enable):
