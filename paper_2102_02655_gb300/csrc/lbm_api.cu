@@ -65,6 +65,7 @@ struct lbm_handle {
     long long step = 0; // steps since lbm_set_geometry
     long long launches = 0;
     int zchunk = 32;
+    int variant = 0;  // fused-kernel configuration (tuning knob CGLBM_FUSED_VARIANT)
     char err[256] = "";
     // event timing (lbm_profile)
     bool profiling = false;
@@ -187,6 +188,10 @@ void fill_geometry(const lbm_handle* h, StepArgs<real>& p, long long n) {
     const long long ri = q20(g.r_inner), ro = q20(g.r_inner + g.wall_thickness);
     p.rin2 = ri * ri;
     p.rout2 = ro * ro;
+    // bounds for "no neighbour can be a wall node": 3/2 l.u. (> sqrt 2) clear
+    const long long rci = q20(std::max(0.0, g.r_inner - 1.5)), rco = q20(g.r_inner + g.wall_thickness + 1.5);
+    p.rclear_in2 = g.r_inner > 1.5 ? rci * rci : -1;
+    p.rclear_out2 = rco * rco;
     p.vn[0] = (real)((double)vx / kFx);
     p.vn[1] = (real)((double)vy / kFx);
     p.vn[2] = real(0);
@@ -328,7 +333,7 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
                 if ((st = mark(h, 1, true, box_sites, h->side)) != LBM_OK) return st;
             }
             if ((st = mark(h, 0, false, 0, h->stream)) != LBM_OK) return st;
-            launched += launch_fused<real>(p, h->zchunk, h->stream);
+            launched += launch_fused<real>(p, h->zchunk, h->stream, h->variant);
             if ((st = mark(h, 0, true, h->N - box_sites, h->stream)) != LBM_OK) return st;
             if (box.wx > 0) {
                 cudaError_t e = cudaEventRecord(h->join, h->side);
@@ -427,13 +432,15 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->N = h->plane * cfg->nz;
     h->esize = cfg->storage == LBM_F64 ? 8 : 4;
     {
-        // z-planes per CTA of the fused kernel: enough CTAs for ~3 per SM,
-        // at least 4 planes so the two-plane prologue stays amortised
+        // z-planes per CTA of the fused kernel: about six waves of two CTAs
+        // per SM (measured best on the 512x128x128 lattice: 16 planes), at
+        // least 4 planes so the two-plane prologue stays amortised
         const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 7) / 8);
-        long long chunks = (152LL * 3 + tiles - 1) / tiles;
+        long long chunks = (152LL * 12 + tiles - 1) / tiles;
         chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));
         h->zchunk = std::max(4, (int)((cfg->nz + chunks - 1) / chunks));
         if (const char* e = getenv("CGLBM_ZCHUNK")) h->zchunk = std::max(1, atoi(e));
+        if (const char* e = getenv("CGLBM_FUSED_VARIANT")) h->variant = atoi(e);
     }
 
     cudaError_t e = cudaSetDevice(cfg->device);

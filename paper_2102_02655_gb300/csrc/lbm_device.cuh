@@ -109,6 +109,7 @@ struct StepArgs {
     // units, reduced into [0, period)
     long long hx[2], hy[2];
     long long rin2, rout2, px, py;  // squared radii (fixed point^2), periods
+    long long rclear_in2, rclear_out2;  // radii 3/2 inside and outside the wall, squared
     real vn[3];        // nozzle velocity (moving-wall rule and node creation)
     real uin[3];       // inlet velocity u_ink + v_nozzle (Eq. 27)
     real utop[3];      // lid velocity
@@ -140,7 +141,9 @@ struct StepArgs {
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+// periodic wrap of any offset; the modulo runs only when a leaves [0, n)
 __device__ __forceinline__ int wrapn(int a, int n) {
+    if (a >= 0 && a < n) return a;
     a %= n;
     return a < 0 ? a + n : a;
 }
@@ -272,10 +275,44 @@ __device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, i
     return kLinkFluid;
 }
 
+// true if no lattice neighbour of (x, y, z) can be a nozzle node of the
+// step-(n-1) geometry: every neighbour lies within sqrt(2) of the site in the
+// x-y plane, so the site's distance to the axis must stay 3/2 clear of the
+// wall's radii (squared radii padded in fixed point), or it lies below gap - 1
+template <typename real>
+__device__ __forceinline__ bool clear_of_nozzle(const StepArgs<real>& p, int x, int y, int z) {
+    if (!p.nozzle || z < p.gap - 1) return true;
+    const long long d2 = axis_d2(p, x, y, 0);
+    return d2 < p.rclear_in2 || d2 > p.rclear_out2;
+}
+
 template <class VS, typename real>
 __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int y, int z, real f[2][VS::Q],
                                              real bc[2]) {
     const long long s = sidx(p, x, y, z);
+    if (p.z_mode == kZPeriodic || (z < p.nz - 1 && clear_of_nozzle(p, x, y, z))) {
+        // plain streaming: every source is a fluid node, except across the
+        // substrate (resting half-way wall, identity on the own population)
+        const int xm = wrapn(x - 1, p.nx), xp = wrapn(x + 1, p.nx);
+        const int ym = wrapn(y - 1, p.ny), yp = wrapn(y + 1, p.ny);
+#pragma unroll
+        for (int i = 0; i < VS::Q; ++i) {
+            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+            int sz = z - cz;
+            long long src;
+            if (p.z_mode == kZPeriodic) sz = wrapn(sz, p.nz);
+            if (sz < 0) {
+                src = s;
+                f[0][i] = p.fin[(long long)opp(i) * p.N + src];
+                f[1][i] = p.fin[(long long)(VS::Q + opp(i)) * p.N + src];
+                continue;
+            }
+            src = sidx(p, cx > 0 ? xm : (cx < 0 ? xp : x), cy > 0 ? ym : (cy < 0 ? yp : y), sz);
+            f[0][i] = p.fin[(long long)i * p.N + src];
+            f[1][i] = p.fin[(long long)(VS::Q + i) * p.N + src];
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < VS::Q; ++i) {
         long long src = 0;

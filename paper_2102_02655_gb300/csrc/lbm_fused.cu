@@ -21,11 +21,15 @@ namespace cglbm {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;  // tile + one-site halo
-constexpr int NRING = HS - NT;                         // 84 halo sites
-constexpr int SX = TX + 4, SY = TY + 4, SS = SX * SY;  // tile + two rings (substrate ghost)
-static_assert(SS - HS <= NT && NRING <= NT, "ring sites must fit one item per thread");
+// Tile geometry: TX x TY sites, one thread each, plus halo rings.
+template <int TY_>
+struct Tile {
+    static constexpr int TX = 32, TY = TY_, NT = TX * TY;
+    static constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;  // tile + one-site halo
+    static constexpr int NRING = HS - NT;                         // halo sites
+    static constexpr int SX = TX + 4, SY = TY + 4, SS = SX * SY;  // tile + two rings (substrate ghost)
+    static_assert(SS - HS <= NT && NRING <= NT, "ring sites must fit one item per thread");
+};
 
 __device__ __forceinline__ int slot_of(int z) { return (z + 3) % 3; }
 
@@ -100,7 +104,7 @@ __device__ __forceinline__ bool in_box(const StepArgs<real>& p, int x, int y, in
     return dx < b.wx && dy < b.wy;
 }
 
-template <typename real, bool kUnit>
+template <typename real, bool kUnit, int HS>
 struct Colour {
     static constexpr int NV = kUnit ? 1 : 3;
     real* col;  // [3 slots][NV][HS]
@@ -120,18 +124,18 @@ struct Colour {
     }
 };
 
-template <typename real, bool kUnit>
+template <typename real, bool kUnit, int HX, int HS>
 struct SmemNb;
-template <typename real>
-struct SmemNb<real, true> {
+template <typename real, int HX, int HS>
+struct SmemNb<real, true, HX, HS> {
     const real* col;
     int slot[3], hidx;
     __device__ __forceinline__ real operator()(int i) const {
         return col[slot[1 + D3Q19::c(i, 2)] * HS + hidx + D3Q19::c(i, 0) + D3Q19::c(i, 1) * HX];
     }
 };
-template <typename real>
-struct SmemNb<real, false> {
+template <typename real, int HX, int HS>
+struct SmemNb<real, false, HX, HS> {
     const real* col;
     int slot[3], hidx;
     __device__ __forceinline__ void operator()(int i, real* cY, real* cB, real* rn) const {
@@ -143,6 +147,7 @@ struct SmemNb<real, false> {
     }
 };
 
+template <int HX, int HY>
 __device__ __forceinline__ void ring_coord(int r, int* hx, int* hy) {
     if (r < HX) { *hx = r; *hy = 0; }
     else if (r < 2 * HX) { *hx = r - HX; *hy = HY - 1; }
@@ -159,13 +164,21 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
     *rB = (p.rho_ref + b) - a;
 }
 
-template <typename real, bool kUnit, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+// kStage: the own sites' pulled populations wait in shared memory for their
+// collision (one plane later); otherwise the collision pulls them again
+// (from L2) and shared memory holds only the colour planes.
+template <typename real, bool kUnit, int TY_, bool kStage, int MINB>
+__global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+    using T = Tile<TY_>;
+    constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
+    constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][38][NT]
-    Colour<real, kUnit> C{pops + 2 * 38 * NT};     // [3 slots][NV][HS]
-    real* sub = pops + 38 * NT;                    // buffer 1, reused by the substrate prologue: [2][SS]
-    // (buffer 1 is first written after the prologue's last read of sub)
+    real* pops = reinterpret_cast<real*>(smraw);   // kStage: [2 buffers][38][NT]
+    Colour<real, kUnit, HS> C{pops + (kStage ? 2 * 38 * NT : 0)};  // [3 slots][NV][HS]
+    // substrate prologue scratch [2][SS]: population buffer 1 (first written
+    // after the prologue's last read of it), or the space after the colours
+    real* sub = kStage ? pops + 38 * NT : C.col + 3 * Colour<real, kUnit, HS>::NV * HS;
+    (void)TX;
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int za = blockIdx.z * zchunk;
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk
                 hy = ty + 2;
             } else if (it == 1) {
                 if (tid >= NRING) continue;
-                ring_coord(tid, &hx, &hy);
+                ring_coord<HX, HY>(tid, &hx, &hy);
                 hx += 1;
                 hy += 1;
             } else {
@@ -205,8 +218,8 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk
             const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
             const bool own = it == 0;
             real f[2][19];
-            pull_fast(p, px, py, zz, f, bc, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
-            if (own && keep && in_xy) {
+            pull_fast(p, px, py, zz, f, bc, kStage && own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
+            if (kStage && own && keep && in_xy) {
                 real* b = pops + (zz & 1) * 38 * NT + tid;
 #pragma unroll
                 for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
@@ -260,10 +273,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
             real f[2][19];
-            const real* b = pops + (z & 1) * 38 * NT + tid;
+            if constexpr (kStage) {
+                const real* b = pops + (z & 1) * 38 * NT + tid;
 #pragma unroll
-            for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
-            SmemNb<real, kUnit> nb{C.col, {slot_of(z - 1), slot_of(z), slot_of(z + 1)}, hidx};
+                for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
+            } else {
+                pull_fast(p, gx, gy, z, f, bc, true);
+            }
+            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), slot_of(z + 1)}, hidx};
             SiteOut<real> so;
             collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
             const int s = z * (int)p.plane + y * p.nx + x;
@@ -308,36 +325,59 @@ __global__ void __launch_bounds__(NT, MINB) k_fused(StepArgs<real> p, int zchunk
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit>
+template <typename real, bool kUnit, int TY_, bool kStage>
 constexpr size_t fused_smem() {
-    return sizeof(real) * (2 * 38 * NT + 3 * Colour<real, kUnit>::NV * HS);
+    using T = Tile<TY_>;
+    const size_t colour = 3 * Colour<real, kUnit, T::HS>::NV * T::HS;
+    return sizeof(real) * (kStage ? 2 * 38 * T::NT + colour : colour + 2 * T::SS);
 }
 
-template <typename real, bool kUnit, int MINB>
+template <typename real, bool kUnit, int TY_, bool kStage, int MINB>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr size_t smem = fused_smem<real, kUnit>();
+    using T = Tile<TY_>;
+    constexpr size_t smem = fused_smem<real, kUnit, TY_, kStage>();
     static unsigned configured = 0;  // one bit per device: the attribute is set once per context
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, kUnit, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused<real, kUnit, TY_, kStage, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         configured |= 1u << dev;
     }
-    dim3 block(TX, TY);
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, kUnit, MINB><<<grid, block, smem, st>>>(p, zchunk);
+    dim3 block(T::TX, T::TY);
+    dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
+    k_fused<real, kUnit, TY_, kStage, MINB><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
+}
+
+template <typename real, int TY_, bool kStage, int MINB>
+int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
+    return p.unit ? launch_one<real, true, TY_, kStage, MINB>(p, zchunk, st)
+                  : launch_one<real, false, TY_, kStage, MINB>(p, zchunk, st);
 }
 
 }  // namespace
 
+// Variant 0 (default): 32 x 8 tiles, populations staged in shared memory, two
+// CTAs per SM. Variants 1-3 exist for tuning measurements (CGLBM_FUSED_VARIANT):
+// 1 = 32 x 16 staged; 2 = 32 x 8 re-pulled, three CTAs per SM; 3 = 32 x 16
+// re-pulled, two CTAs per SM. FP64 always uses variant 0 with one CTA per SM.
 template <typename real>
-int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr int MINB = sizeof(real) == 4 ? 2 : 1;
-    return p.unit ? launch_one<real, true, MINB>(p, zchunk, st) : launch_one<real, false, MINB>(p, zchunk, st);
+int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
+    if constexpr (sizeof(real) == 8) {
+        (void)variant;
+        return launch_variant<real, 8, true, 1>(p, zchunk, st);
+    } else {
+        switch (variant) {
+        case 1: return launch_variant<real, 16, true, 1>(p, zchunk, st);
+        case 2: return launch_variant<real, 8, false, 3>(p, zchunk, st);
+        case 3: return launch_variant<real, 16, false, 2>(p, zchunk, st);
+        default: return launch_variant<real, 8, true, 2>(p, zchunk, st);
+        }
+    }
 }
 
-template int launch_fused<float>(const StepArgs<float>&, int, cudaStream_t);
-template int launch_fused<double>(const StepArgs<double>&, int, cudaStream_t);
+template int launch_fused<float>(const StepArgs<float>&, int, cudaStream_t, int);
+template int launch_fused<double>(const StepArgs<double>&, int, cudaStream_t, int);
 
 }  // namespace cglbm

@@ -18,8 +18,9 @@ template <class VS, typename real>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st);
 
 // Fused bulk step over every site outside p.box (D3Q19, substrate + open top).
+// variant selects a tile/staging configuration (0 = default).
 template <typename real>
-int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st);
+int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant);
 
 // Equilibrium initialisation from fields staged in p.fields (rho_ink, rho_amb,
 // ux, uy, uz planes; u optional) or, when staged == 0, from the print-setup

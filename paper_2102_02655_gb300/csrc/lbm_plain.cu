@@ -11,16 +11,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ bool region_site(const Region& r, long long t, int nx, int ny, int* x, int* y, int* z) {
-    const long long nxy = (long long)r.wx * r.wy;
-    if (t >= nxy * (r.z1 - r.z0)) return false;
-    const int zz = (int)(t / nxy);
-    const long long rem = t - (long long)zz * nxy;
-    const int j = (int)(rem / r.wx);
-    const int i = (int)(rem - (long long)j * r.wx);
+// Launch shape of a region: blockIdx.x covers the region's columns (32-bit),
+// blockIdx.y its planes. Returns false for threads past the last column.
+__device__ __forceinline__ bool region_site(const Region& r, int nx, int ny, int* x, int* y, int* z) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= r.wx * r.wy) return false;
+    const int j = t / r.wx;
+    const int i = t - j * r.wx;
     *x = wrapn(r.x0 + i, nx);
     *y = wrapn(r.y0 + j, ny);
-    *z = r.z0 + zz;
+    *z = r.z0 + (int)blockIdx.y;
     return true;
 }
 
@@ -48,17 +48,19 @@ inline int blocks_for(long long n) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// one thread per column of the region, one grid row per plane
+inline dim3 region_grid(const Region& r) {
+    const long long cols = (long long)r.wx * r.wy;
+    return dim3((unsigned)((cols + kThreads - 1) / kThreads), (unsigned)(r.z1 - r.z0 > 0 ? r.z1 - r.z0 : 1));
+}
+
 // 1. stream + densities (post-streaming) of every fluid node of step n-1 in R2
 template <class VS, typename real>
-__global__ void __launch_bounds__(kThreads) k_stream_density(StepArgs<real> p, Region R2, Region R) {
+__global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p, Region R2, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double bc0 = 0, bc1 = 0, de0 = 0, de1 = 0;
-    const long long total = region_sites(R2);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        region_site(R2, t, p.nx, p.ny, &x, &y, &z);
-        if (solid_at(p, x, y, z, 0)) continue;
+    int x, y, z;
+    if (region_site(R2, p.nx, p.ny, &x, &y, &z) && !solid_at(p, x, y, z, 0)) {
         real f[2][VS::Q];
         real bc[2] = {real(0), real(0)};
         pull_general<VS>(p, x, y, z, f, bc);
@@ -72,7 +74,18 @@ __global__ void __launch_bounds__(kThreads) k_stream_density(StepArgs<real> p, R
         if (in_region(R, x, y, z, p.nx, p.ny)) {
             bc0 += (double)bc[0];
             bc1 += (double)bc[1];
-            if (solid_at(p, x, y, z, 1)) { de0 += (double)rY; de1 += (double)rB; }
+            if (solid_at(p, x, y, z, 1)) {
+                de0 += (double)rY;
+                de1 += (double)rB;
+            } else {
+                // the collision of this site reads these in place (step 4)
+                const long long s = sidx(p, x, y, z);
+#pragma unroll
+                for (int i = 0; i < VS::Q; ++i) {
+                    p.fout[(long long)i * p.N + s] = f[0][i];
+                    p.fout[(long long)(VS::Q + i) * p.N + s] = f[1][i];
+                }
+            }
         }
     }
     warp_add(p.acc + kAccBc, bc0);
@@ -87,12 +100,8 @@ template <class VS, typename real>
 __global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R1, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double c0 = 0, c1 = 0;
-    const long long total = region_sites(R1);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        region_site(R1, t, p.nx, p.ny, &x, &y, &z);
-        if (!(solid_at(p, x, y, z, 0) && !solid_at(p, x, y, z, 1))) continue;
+    int x, y, z;
+    if (region_site(R1, p.nx, p.ny, &x, &y, &z) && solid_at(p, x, y, z, 0) && !solid_at(p, x, y, z, 1)) {
         real s0 = 0, s1 = 0;
         int cnt = 0;
 #pragma unroll
@@ -113,7 +122,20 @@ __global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R
         const long long r = ridx(p, x, y, z);
         p.rho_cur[r] = m0;
         p.rho_cur[comp + r] = m1;
-        if (in_region(R, x, y, z, p.nx, p.ny)) { c0 += (double)m0; c1 += (double)m1; }
+        if (in_region(R, x, y, z, p.nx, p.ny)) {
+            c0 += (double)m0;
+            c1 += (double)m1;
+            // populations of the created node: equilibrium at the nozzle velocity
+            const long long s = sidx(p, x, y, z);
+            const real uu = p.vn[0] * p.vn[0] + p.vn[1] * p.vn[1] + p.vn[2] * p.vn[2];
+#pragma unroll
+            for (int i = 0; i < VS::Q; ++i) {
+                real eY, eD;
+                feq_pair<VS>(p, i, m0, m1, p.vn[0], p.vn[1], p.vn[2], uu, &eY, &eD);
+                p.fout[(long long)i * p.N + s] = eY;
+                p.fout[(long long)(VS::Q + i) * p.N + s] = eD;
+            }
+        }
     }
     warp_add(p.acc + kAccCreated, c0);
     warp_add(p.acc + kAccCreated + 1, c1);
@@ -146,14 +168,12 @@ __device__ __forceinline__ void wall_rho(const StepArgs<real>& p, int x, int y, 
 template <class VS, typename real>
 __global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g) {
     const long long comp = p.N + 2 * p.plane;
-    const long long total = region_sites(R1g);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        region_site(R1g, t, p.nx, p.ny, &x, &y, &z);
+    int x, y, z;
+    if (!region_site(R1g, p.nx, p.ny, &x, &y, &z)) return;
+    {
         real o0, o1;
         if (z < 0 || z >= p.nz) {
-            if (p.z_mode != kZWalls) continue;
+            if (p.z_mode != kZWalls) return;
             if (z >= p.nz && p.top_mode == kTopOpen) {
                 // open top: zero normal gradient, copy of the top plane
                 const int zt = p.nz - 1;
@@ -168,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g)
                 wall_rho<VS>(p, x, y, z, &o0, &o1);  // substrate or lid
             }
         } else {
-            if (!solid_at(p, x, y, z, 1)) continue;
+            if (!solid_at(p, x, y, z, 1)) return;
             wall_rho<VS>(p, x, y, z, &o0, &o1);
         }
         const long long r = ridx(p, x, y, z);
@@ -227,41 +247,31 @@ __device__ __forceinline__ void store_fields(const StepArgs<real>& p, long long 
     F[kFSolid * p.N + s] = solid;
 }
 
-// 4. collision at every fluid node of step n in R
-template <class VS, typename real>
-__global__ void __launch_bounds__(kThreads) k_collide(StepArgs<real> p, Region R) {
+// 4. collision at every fluid node of step n in R, in place: steps 1 and 2
+//    left the post-streaming (or created) populations in fout
+template <class VS, typename real, bool kUnit>
+__global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double m0 = 0, m1 = 0, px = 0, py = 0, pz = 0;
     int bad = 0;
-    const long long total = region_sites(R);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        region_site(R, t, p.nx, p.ny, &x, &y, &z);
-        const long long s = sidx(p, x, y, z);
-        if (solid_at(p, x, y, z, 1)) {
-            if (p.write_fields) {
-                SiteOut<real> so = {0, 0, {0, 0, 0}, 0, 0};
-                store_fields(p, s, so, real(1));
-            }
-            continue;
+    int x, y, z;
+    const bool active = region_site(R, p.nx, p.ny, &x, &y, &z);
+    const long long s = active ? sidx(p, x, y, z) : 0;
+    if (active && solid_at(p, x, y, z, 1)) {
+        if (p.write_fields) {
+            SiteOut<real> so = {0, 0, {0, 0, 0}, 0, 0};
+            store_fields(p, s, so, real(1));
         }
+    } else if (active) {
         real f[2][VS::Q];
-        if (solid_at(p, x, y, z, 0)) {
-            // created node: equilibrium at the nozzle velocity (Sec. II B)
-            const long long r = ridx(p, x, y, z);
-            const real r0 = p.rho_cur[r], r1 = p.rho_cur[comp + r];
-            const real uu = p.vn[0] * p.vn[0] + p.vn[1] * p.vn[1] + p.vn[2] * p.vn[2];
 #pragma unroll
-            for (int i = 0; i < VS::Q; ++i)
-                feq_pair<VS>(p, i, r0, r1, p.vn[0], p.vn[1], p.vn[2], uu, &f[0][i], &f[1][i]);
-        } else {
-            real bc[2] = {real(0), real(0)};
-            pull_general<VS>(p, x, y, z, f, bc);
+        for (int i = 0; i < VS::Q; ++i) {
+            f[0][i] = p.fout[(long long)i * p.N + s];
+            f[1][i] = p.fout[(long long)(VS::Q + i) * p.N + s];
         }
         SiteOut<real> so;
         const real zd = p.z_mode == kZWalls ? real(z) + real(0.5) : real(-1);
-        if (p.unit) {
+        if constexpr (kUnit) {
             ArrayNbUnit<VS, real> nb{&p, x, y, z};
             collide<VS, real, true>(p, f, nb, zd, &so);
         } else {
@@ -405,15 +415,16 @@ template int launch_prev_from_f<D2Q9, double>(const StepArgs<double>&, double*, 
 template <class VS, typename real>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st) {
     if (region_sites(R) == 0) return 0;
-    k_stream_density<VS, real><<<blocks_for(region_sites(R2)), kThreads, 0, st>>>(p, R2, R);
-    k_created<VS, real><<<blocks_for(region_sites(R1)), kThreads, 0, st>>>(p, R1, R);
+    k_stream_density<VS, real><<<region_grid(R2), kThreads, 0, st>>>(p, R2, R);
+    k_created<VS, real><<<region_grid(R1), kThreads, 0, st>>>(p, R1, R);
     Region R1g = R1;
     if (p.z_mode == kZWalls) {
         if (R1g.z0 <= 0) R1g.z0 = -1;
         if (R1g.z1 >= p.nz) R1g.z1 = p.nz + 1;
     }
-    k_wall<VS, real><<<blocks_for(region_sites(R1g)), kThreads, 0, st>>>(p, R1g);
-    k_collide<VS, real><<<blocks_for(region_sites(R)), kThreads, 0, st>>>(p, R);
+    k_wall<VS, real><<<region_grid(R1g), kThreads, 0, st>>>(p, R1g);
+    if (p.unit) k_collide<VS, real, true><<<region_grid(R), kThreads, 0, st>>>(p, R);
+    else k_collide<VS, real, false><<<region_grid(R), kThreads, 0, st>>>(p, R);
     return 4;
 }
 
