@@ -83,6 +83,20 @@ struct D2Q9 {
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// Link vectors for loops that index the velocity set at run time (the
+// compact boundary path); same order as the constexpr tables above.
+static __constant__ signed char kLinkD3Q19[19][3] = {
+    {0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+static __constant__ signed char kLinkD2Q9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 0, 1}, {0, 0, -1},
+                                                   {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}};
+template <class VS>
+__device__ __forceinline__ int link(int i, int a) {
+    if constexpr (VS::Q == 19) return kLinkD3Q19[i][a];
+    else return kLinkD2Q9[i][a];
+}
+
 enum { kZPeriodic = 0, kZWalls = 1 };
 enum { kTopOpen = 0, kTopWall = 1 };
 enum { kLawNewtonian = 0, kLawCross = 1, kLawPower = 2 };
@@ -195,16 +209,16 @@ __device__ __forceinline__ bool solid_at(const StepArgs<real>& p, int x, int y, 
 // bc[k] accumulates the mass change of the boundary links.
 // ---------------------------------------------------------------------------
 
-template <class VS, typename real>
-__device__ __forceinline__ real wall_density(const StepArgs<real>& p, int k, int x, int y, int z, int i,
-                                             long long s_self) {
+template <typename real>
+__device__ __forceinline__ real wall_density(const StepArgs<real>& p, int k, int x, int y, int z, int cx, int cy,
+                                             int cz, long long s_self) {
     // Eq. 26: density at the wall by quadratic extrapolation along +c_i from
     // x (distance 1/2), x + c_i (3/2), x + 2 c_i (5/2), using the step-(n-1)
     // densities; falls back to the node's own density if either is not fluid.
     const real r0 = p.rho_prev[(long long)k * (p.N + 2 * p.plane) + s_self + p.plane];
-    const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
-    const int x2 = wrapn(x + 2 * VS::c(i, 0), p.nx), y2 = wrapn(y + 2 * VS::c(i, 1), p.ny);
-    int z1 = z + VS::c(i, 2), z2 = z + 2 * VS::c(i, 2);
+    const int x1 = wrapn(x + cx, p.nx), y1 = wrapn(y + cy, p.ny);
+    const int x2 = wrapn(x + 2 * cx, p.nx), y2 = wrapn(y + 2 * cy, p.ny);
+    int z1 = z + cz, z2 = z + 2 * cz;
     if (p.z_mode == kZPeriodic) {
         z1 = wrapn(z1, p.nz);
         z2 = wrapn(z2, p.nz);
@@ -224,25 +238,26 @@ __device__ __forceinline__ long long utop_idx(const StepArgs<real>& p, int a, in
     return ((long long)a * 2 + (z - (p.nz - 2))) * p.plane + (long long)y * p.nx + x;
 }
 
-template <class VS, typename real>
-__device__ __forceinline__ void anti_bb_velocity(const StepArgs<real>& p, int x, int y, int z, int i, real uw[3]) {
+template <typename real>
+__device__ __forceinline__ void anti_bb_velocity(const StepArgs<real>& p, int x, int y, int z, int cx, int cy, int cz,
+                                                 real uw[3]) {
     // Eq. 28: half-way velocity by second-order extrapolation
     // 1.5 u(x) - 0.5 u(x + c_i), step n-1 values; u(x) alone if x + c_i is not fluid
     for (int a = 0; a < 3; ++a) uw[a] = p.u_prev[utop_idx(p, a, x, y, z)];
-    const int z1 = z + VS::c(i, 2);
+    const int z1 = z + cz;
     if (z1 < 0 || z1 < p.nz - 2) return;
-    const int x1 = wrapn(x + VS::c(i, 0), p.nx), y1 = wrapn(y + VS::c(i, 1), p.ny);
+    const int x1 = wrapn(x + cx, p.nx), y1 = wrapn(y + cy, p.ny);
     if (solid_at(p, x1, y1, z1, 0)) return;
     for (int a = 0; a < 3; ++a) uw[a] = real(1.5) * uw[a] - real(0.5) * p.u_prev[utop_idx(p, a, x1, y1, z1)];
 }
 
 enum { kLinkFluid = 0, kLinkRest, kLinkMoving, kLinkOpen };
 
-template <class VS, typename real>
-__device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, int z, int i, long long* src,
-                                        real uw[3]) {
-    const int sx = wrapn(x - VS::c(i, 0), p.nx), sy = wrapn(y - VS::c(i, 1), p.ny);
-    int sz = z - VS::c(i, 2);
+template <typename real>
+__device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, int z, int cx, int cy, int cz,
+                                        long long* src, real uw[3]) {
+    const int sx = wrapn(x - cx, p.nx), sy = wrapn(y - cy, p.ny);
+    int sz = z - cz;
     uw[0] = uw[1] = uw[2] = real(0);
     if (p.z_mode == kZPeriodic) {
         *src = sidx(p, sx, sy, wrapn(sz, p.nz));
@@ -313,11 +328,14 @@ __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int
         }
         return;
     }
-#pragma unroll
+    // near the nozzle or on the top plane: every link classified, in a
+    // compact loop (this path is rare; its code stays small)
+#pragma unroll 1
     for (int i = 0; i < VS::Q; ++i) {
+        const int cx = link<VS>(i, 0), cy = link<VS>(i, 1), cz = link<VS>(i, 2);
         long long src = 0;
         real uw[3];
-        const int kind = classify<VS>(p, x, y, z, i, &src, uw);
+        const int kind = classify(p, x, y, z, cx, cy, cz, &src, uw);
         const int ib = opp(i);
         if (kind == kLinkFluid) {
             f[0][i] = p.fin[(long long)i * p.N + src];
@@ -333,16 +351,16 @@ __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int
             vD = oD;
         } else if (kind == kLinkMoving) {
             // Eq. 26 per component; for the total the wall densities add up
-            const real rwY = wall_density<VS>(p, 0, x, y, z, i, s);
-            const real rwB = wall_density<VS>(p, 1, x, y, z, i, s);
-            const real ucb = -((real)VS::c(i, 0) * uw[0] + (real)VS::c(i, 1) * uw[1] + (real)VS::c(i, 2) * uw[2]);
+            const real rwY = wall_density(p, 0, x, y, z, cx, cy, cz, s);
+            const real rwB = wall_density(p, 1, x, y, z, cx, cy, cz, s);
+            const real ucb = -((real)cx * uw[0] + (real)cy * uw[1] + (real)cz * uw[2]);
             vY = oY - real(6) * w * rwY * ucb;
             vD = oD - real(6) * w * (rwY + rwB) * ucb;
         } else {
             // Eq. 28 with imposed densities 0 (ink) and rho_top (ambient)
             real u2[3];
-            anti_bb_velocity<VS>(p, x, y, z, i, u2);
-            const real cu = (real)VS::c(ib, 0) * u2[0] + (real)VS::c(ib, 1) * u2[1] + (real)VS::c(ib, 2) * u2[2];
+            anti_bb_velocity(p, x, y, z, cx, cy, cz, u2);
+            const real cu = -((real)cx * u2[0] + (real)cy * u2[1] + (real)cz * u2[2]);  // c_ib . u
             const real uu = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
             const real q = real(4.5) * cu * cu - real(1.5) * uu;
             vY = -oY;
