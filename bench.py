@@ -47,6 +47,34 @@ def _dist():
     return ws, rank, local
 
 
+# Replica bookkeeping for N > 1 (one independent lattice per rank, no
+# data-path collective): a barrier around the timed region, the slowest
+# rank's time, and the whole-job rate over every rank's sites.
+
+def replica_barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(v, ws, device):
+    """Maximum of a per-rank float over all ranks (the slowest rank's time)."""
+    if ws == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(ws, sites_per_rank, steps, ms):
+    """Whole-job site updates per second (millions) when each of ws ranks
+    advances its own lattice of sites_per_rank sites by steps steps and the
+    slowest rank took ms milliseconds."""
+    return ws * sites_per_rank * steps / (ms * 1e-3) / 1e6
+
+
 class Clocks:
     """nvidia-smi samples of the SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -185,15 +213,10 @@ def run_ours(args):
     stream = lat.stream
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        replica_barrier(ws)
 
     def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, ws, "cuda")
 
     # warm-up
     lat.step(args.warmup)
@@ -217,7 +240,7 @@ def run_ours(args):
     tm = lat.timings()
     lat.profile(False)
     ms = max_over_ranks(ms)
-    value = ws * nsites * args.steps / (ms * 1e-3) / 1e6
+    value = aggregate_mlups(ws, nsites, args.steps, ms)
 
     # roofline of the dominant kernel (fused bulk kernel)
     peak, peak_kind = _peaks()
@@ -283,7 +306,7 @@ def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
                      out=[o.numpy() for o in outs])
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     esz = 4 if storage == "f32" else 8
-    e2e = {"value": ws * nsites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": aggregate_mlups(ws, nsites, args.steps, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": 2 * nsites * esz / args.steps,
            "d2h_bytes_per_step": (5 * nsites * esz + 120) / args.steps,
            "what": "per request: pinned H2D of rho_ink, rho_amb; K steps; D2H of rho_ink, rho_amb, u, diag"}
