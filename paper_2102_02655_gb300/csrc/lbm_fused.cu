@@ -9,8 +9,10 @@
 //     collision of that plane (one iteration later), and their densities;
 //   - the densities of the one-site halo ring around the tile (these re-reads
 //     of neighbouring tiles' populations are served by L2);
-// and keeps three planes of colour fractions in shared memory. HBM traffic is
-// one read and one write of the populations per site update.
+// and keeps four planes of colour fractions in shared memory (a ring: the
+// plane written for z + 1 is never one that a collision of plane z - 1 still
+// reads, so one barrier per plane suffices). HBM traffic is one read and one
+// write of the populations per site update.
 //
 // Indices are 32-bit (the host selects this kernel only when 38 N < 2^31);
 // the periodic wrap in x and y is resolved once per site into the source
@@ -31,16 +33,54 @@ struct Tile {
     static_assert(SS - HS <= NT && NRING <= NT, "ring sites must fit one item per thread");
 };
 
-__device__ __forceinline__ int slot_of(int z) { return (z + 3) % 3; }
+__device__ __forceinline__ int slot_of(int z) { return (z + 4) & 3; }  // z >= -1
 
-// streaming for a site away from the nozzle: every source is fluid except
-// across the substrate (resting half-way wall) and the open top
-// (anti-bounce-back, Eq. 28, with the velocity extrapolated from the last two
-// planes of the previous step). ledger adds the boundary-link mass changes.
+// Streaming for a site away from the nozzle on a plane below the top
+// (0 <= zz <= nz - 2): every source is a fluid site except across the
+// substrate, where the resting half-way wall bounces the population back
+// (the pull then reads the opposite direction at the site itself). Branch-free:
+// the substrate case is an address select on the upward directions only.
 template <typename real>
-__device__ __forceinline__ void pull_fast(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19],
-                                          double bc[2], bool ledger) {
+__device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19]) {
     using VS = D3Q19;
+    const int nx = p.nx, ny = p.ny, pl = (int)p.plane, N = (int)p.N;
+    const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+    const int r0 = gy * nx;
+    const int rm = (gy == 0 ? ny - 1 : gy - 1) * nx, rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
+    const int s = zz * pl + r0 + gx;
+    const bool bottom = zz == 0;
+    const real* fin = p.fin;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
+        const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
+        int idx = i * N + zz * pl - cz * pl + sy + sx;
+        if (cz > 0) idx = bottom ? opp(i) * N + s : idx;
+        f[0][i] = fin[idx];
+        f[1][i] = fin[idx + 19 * N];
+    }
+}
+
+// Streaming on the top plane (zz = nz - 1; also the substrate when nz = 1):
+// links leaving through the open top take the anti-bounce-back value of
+// Eq. 28 with rho_Y = 0 and rho_B = rho_top, the wall velocity extrapolated
+// from the last two planes of the previous step, u_w = 1.5 u(x) - 0.5 u(x + c_i).
+// Stores the 38 populations to
+// dst[i * stride] when dst is set, and returns the densities after streaming
+// and, when ledger, the boundary-link mass change of each component. A rolled
+// loop over a run-time link table: it runs on one plane in nz, so it is kept
+// small rather than fast.
+template <typename real>
+struct TopPull {
+    real rY, rB;
+    double b0, b1;
+};
+template <typename real>
+__device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int gx, int gy, real* dst, int stride,
+                                                  bool ledger) {
+    using VS = D3Q19;
+    const int zz = p.nz - 1;
     const int nx = p.nx, ny = p.ny, pl = (int)p.plane, N = (int)p.N;
     const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
     const int r0 = gy * nx;
@@ -48,43 +88,51 @@ __device__ __forceinline__ void pull_fast(const StepArgs<real>& p, int gx, int g
     const int zoff = zz * pl;
     const int s = zoff + r0 + gx;
     const real* fin = p.fin;
-#pragma unroll
+    TopPull<real> r{real(0), real(0), 0.0, 0.0};
+    real sumD = 0;
+#pragma unroll 1
     for (int i = 0; i < 19; ++i) {
-        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        const int cx = link<VS>(i, 0), cy = link<VS>(i, 1), cz = link<VS>(i, 2);
         const int sz = zz - cz;
         const int ib = opp(i);
+        real fY, fD;
         if (sz < 0) {
-            f[0][i] = fin[ib * N + s];
-            f[1][i] = fin[(19 + ib) * N + s];
+            fY = fin[ib * N + s];
+            fD = fin[(19 + ib) * N + s];
         } else if (sz >= p.nz) {
-            // u_w = 1.5 u(x) - 0.5 u(x + c_i): the velocity of the last two
-            // planes of the previous step ([component][plane nz-2, nz-1][site])
             real uw[3];
             const int x1 = cx > 0 ? xp : (cx < 0 ? xm : gx), y1 = cy > 0 ? rp : (cy < 0 ? rm : r0);
-#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const real u0 = p.u_prev[a * 2 * pl + pl + r0 + gx];
                 uw[a] = p.nz >= 2 ? real(1.5) * u0 - real(0.5) * p.u_prev[a * 2 * pl + y1 + x1] : u0;
             }
-            const real cu = (real)VS::c(ib, 0) * uw[0] + (real)VS::c(ib, 1) * uw[1] + (real)VS::c(ib, 2) * uw[2];
+            const real cu = -(real)(cx * uw[0] + cy * uw[1] + cz * uw[2]);  // c_ib . u_w
             const real q = real(4.5) * cu * cu - real(1.5) * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
-            const real w = (real)VS::w(ib);
+            const real w = (real)(VS::w(1) * (i <= 6) + VS::w(7) * (i > 6));
             const real oY = fin[ib * N + s];
             const real oD = fin[(19 + ib) * N + s];
-            f[0][i] = -oY;  // imposed ink density 0
-            f[1][i] = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
+            fY = -oY;  // imposed ink density 0
+            fD = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
             if (ledger) {
-                bc[0] += (double)(f[0][i] - oY);
-                bc[1] += (double)((f[1][i] - oD) - (f[0][i] - oY));
+                r.b0 += (double)(fY - oY);
+                r.b1 += (double)((fD - oD) - (fY - oY));
             }
         } else {
             const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
             const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
             const int src = zoff - cz * pl + sy + sx;
-            f[0][i] = fin[i * N + src];
-            f[1][i] = fin[(19 + i) * N + src];
+            fY = fin[i * N + src];
+            fD = fin[(19 + i) * N + src];
         }
+        if (dst) {
+            dst[i * stride] = fY;
+            dst[(19 + i) * stride] = fD;
+        }
+        r.rY += fY;
+        sumD += fD;
     }
+    r.rB = (p.rho_ref + sumD) - r.rY;
+    return r;
 }
 
 __device__ __forceinline__ void warp_add(double* dst, double v) {
@@ -117,10 +165,6 @@ struct Colour {
             col[(slot * 3 + 1) * HS + j] = rB * inv;
             col[(slot * 3 + 2) * HS + j] = phase_field(p, rY, rB);
         }
-    }
-    __device__ __forceinline__ void copy(int dst, int src, int j) const {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) col[(dst * NV + v) * HS + j] = col[(src * NV + v) * HS + j];
     }
 };
 
@@ -164,20 +208,19 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
     *rB = (p.rho_ref + b) - a;
 }
 
-// kStage: the own sites' pulled populations wait in shared memory for their
-// collision (one plane later); otherwise the collision pulls them again
-// (from L2) and shared memory holds only the colour planes.
-template <typename real, bool kUnit, int TY_, bool kStage, int MINB>
+// The own sites' pulled populations wait in shared memory for their
+// collision (one plane later); each thread reads back only its own column.
+template <typename real, bool kUnit, int TY_, int MINB>
 __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     using T = Tile<TY_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    real* pops = reinterpret_cast<real*>(smraw);   // kStage: [2 buffers][38][NT]
-    Colour<real, kUnit, HS> C{pops + (kStage ? 2 * 38 * NT : 0)};  // [3 slots][NV][HS]
-    // substrate prologue scratch [2][SS]: population buffer 1 (first written
-    // after the prologue's last read of it), or the space after the colours
-    real* sub = kStage ? pops + 38 * NT : C.col + 3 * Colour<real, kUnit, HS>::NV * HS;
+    real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][38][NT]
+    Colour<real, kUnit, HS> C{pops + 2 * 38 * NT};  // [4 slots][NV][HS]
+    // substrate prologue scratch [2][SS]: population buffer 1, first written
+    // after the prologue's last read of it
+    real* sub = pops + 38 * NT;
     (void)TX;
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -217,15 +260,24 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
             }
             const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
             const bool own = it == 0;
-            real f[2][19];
-            pull_fast(p, px, py, zz, f, bc, kStage && own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
-            if (kStage && own && keep && in_xy) {
-                real* b = pops + (zz & 1) * 38 * NT + tid;
-#pragma unroll
-                for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
-            }
+            real* dst = own && keep ? pops + (zz & 1) * 38 * NT + tid : nullptr;
             real rY, rB;
-            density(f, p, &rY, &rB);
+            if (zz == p.nz - 1) {
+                const TopPull<real> r =
+                    pull_top(p, px, py, dst, NT, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
+                rY = r.rY;
+                rB = r.rB;
+                bc[0] += r.b0;
+                bc[1] += r.b1;
+            } else {
+                real f[2][19];
+                pull_interior(p, px, py, zz, f);
+                if (dst) {
+#pragma unroll
+                    for (int i = 0; i < 38; ++i) dst[i * NT] = f[i / 19][i % 19];
+                }
+                density(f, p, &rY, &rB);
+            }
             if (outer) {
                 sub[hy * SX + hx] = rY;
                 sub[SS + hy * SX + hx] = rB;
@@ -253,8 +305,9 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
                 n1 += w * sub[SS + cc];
                 den += w;
             }
-            C.put(p, 2, j, p.zeta[0] * n0 / den, p.zeta[1] * n1 / den);  // plane -1
+            C.put(p, slot_of(-1), j, p.zeta[0] * n0 / den, p.zeta[1] * n1 / den);
         }
+        __syncthreads();  // the scratch in buffer 1 is read; plane 1 goes there next
     } else {
         load_plane(za - 1, false, false);
         load_plane(za, true, false);
@@ -263,24 +316,22 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
     double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
     int bad = 0;
     for (int z = za; z < zb; ++z) {
-        __syncthreads();  // plane z-2's colour slot and population buffer are free
-        if (z + 1 < p.nz) {
-            load_plane(z + 1, true, false);
-        } else {
-            // open top: zero normal gradient, the ghost plane copies the top plane
-            for (int j = tid; j < HS; j += NT) C.copy(slot_of(z + 1), slot_of(z), j);
-        }
+        // plane z + 1 goes to colour slot (z + 1) mod 4 and population buffer
+        // (z + 1) & 1: no collision still running (plane z - 1, other threads)
+        // reads that slot, and the buffer's previous plane was read by this
+        // thread only
+        if (z + 1 < p.nz) load_plane(z + 1, true, false);
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
             real f[2][19];
-            if constexpr (kStage) {
+            {
                 const real* b = pops + (z & 1) * 38 * NT + tid;
 #pragma unroll
                 for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
-            } else {
-                pull_fast(p, gx, gy, z, f, bc, true);
             }
-            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), slot_of(z + 1)}, hidx};
+            // open top: zero normal gradient, the ghost plane above is the top plane
+            const int sup = z + 1 < p.nz ? slot_of(z + 1) : slot_of(z);
+            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx};
             SiteOut<real> so;
             collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
             const int s = z * (int)p.plane + y * p.nx + x;
@@ -325,55 +376,48 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int TY_, bool kStage>
+template <typename real, bool kUnit, int TY_>
 constexpr size_t fused_smem() {
     using T = Tile<TY_>;
-    const size_t colour = 3 * Colour<real, kUnit, T::HS>::NV * T::HS;
-    return sizeof(real) * (kStage ? 2 * 38 * T::NT + colour : colour + 2 * T::SS);
+    return sizeof(real) * (2 * 38 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, bool kUnit, int TY_, bool kStage, int MINB>
+template <typename real, bool kUnit, int TY_, int MINB>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     using T = Tile<TY_>;
-    constexpr size_t smem = fused_smem<real, kUnit, TY_, kStage>();
+    constexpr size_t smem = fused_smem<real, kUnit, TY_>();
+    static_assert(smem <= 227 * 1024, "shared memory of one CTA");
     static unsigned configured = 0;  // one bit per device: the attribute is set once per context
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, kUnit, TY_, kStage, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_fused<real, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, kUnit, TY_, kStage, MINB><<<grid, block, smem, st>>>(p, zchunk);
+    k_fused<real, kUnit, TY_, MINB><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
-template <typename real, int TY_, bool kStage, int MINB>
+template <typename real, int TY_, int MINB>
 int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, true, TY_, kStage, MINB>(p, zchunk, st)
-                  : launch_one<real, false, TY_, kStage, MINB>(p, zchunk, st);
+    return p.unit ? launch_one<real, true, TY_, MINB>(p, zchunk, st)
+                  : launch_one<real, false, TY_, MINB>(p, zchunk, st);
 }
 
 }  // namespace
 
-// Variant 0 (default): 32 x 8 tiles, populations staged in shared memory, two
-// CTAs per SM. Variants 1-3 exist for tuning measurements (CGLBM_FUSED_VARIANT):
-// 1 = 32 x 16 staged; 2 = 32 x 8 re-pulled, three CTAs per SM; 3 = 32 x 16
-// re-pulled, two CTAs per SM. FP64 always uses variant 0 with one CTA per SM.
+// Variant 0 (default): 32 x 8 tiles, two CTAs per SM (one in FP64). Variant 1
+// (tuning measurements, CGLBM_FUSED_VARIANT=1): 32 x 16 tiles, one CTA per SM.
 template <typename real>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
         (void)variant;
-        return launch_variant<real, 8, true, 1>(p, zchunk, st);
+        return launch_variant<real, 8, 1>(p, zchunk, st);
     } else {
-        switch (variant) {
-        case 1: return launch_variant<real, 16, true, 1>(p, zchunk, st);
-        case 2: return launch_variant<real, 8, false, 3>(p, zchunk, st);
-        case 3: return launch_variant<real, 16, false, 2>(p, zchunk, st);
-        default: return launch_variant<real, 8, true, 2>(p, zchunk, st);
-        }
+        if (variant == 1) return launch_variant<real, 16, 1>(p, zchunk, st);
+        return launch_variant<real, 8, 2>(p, zchunk, st);
     }
 }
 
