@@ -396,12 +396,35 @@ __device__ __forceinline__ double rpow<double>(double a, double b) { return pow(
 template <>
 __device__ __forceinline__ float rpow<float>(float a, float b) { return powf(a, b); }
 
+// Quotient, square root and reciprocal square root for the collision's smooth
+// coefficients (velocity, colour fraction, mixture viscosity, perturbation and
+// recolouring amplitudes). FP64 keeps the IEEE operations; FP32 takes the
+// hardware approximations (within 2 ulp), far below the FP32 storage rounding
+// that already bounds the single-precision path.
 template <typename real>
-__device__ __forceinline__ real rsqrt_(real a);
+__device__ __forceinline__ real qdiv(real a, real b);
 template <>
-__device__ __forceinline__ double rsqrt_<double>(double a) { return sqrt(a); }
+__device__ __forceinline__ double qdiv<double>(double a, double b) { return a / b; }
 template <>
-__device__ __forceinline__ float rsqrt_<float>(float a) { return sqrtf(a); }
+__device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename real>
+__device__ __forceinline__ real qrsqrt(real a);  // a > 0
+template <>
+__device__ __forceinline__ double qrsqrt<double>(double a) { return 1.0 / sqrt(a); }
+template <>
+__device__ __forceinline__ float qrsqrt<float>(float a) { return rsqrtf(a); }
+
+template <typename real>
+__device__ __forceinline__ real qsqrt(real a);  // a >= 0
+template <>
+__device__ __forceinline__ double qsqrt<double>(double a) { return sqrt(a); }
+template <>
+__device__ __forceinline__ float qsqrt<float>(float a) { return a > 0.0f ? a * rsqrtf(a) : 0.0f; }
+
+// ink fraction rho_Y / (rho_Y + rho_B) of a site's densities
+template <typename real>
+__device__ __forceinline__ real colour_frac(real a, real b) { return qdiv(a, a + b); }
 
 // tau of the ink law at shear rate g (unclamped) and d tau / d g
 template <typename real>
@@ -518,7 +541,7 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     }
     const real rho = p.rho_ref + sd;
     const real rB = rho - rY;
-    const real irho = real(1) / rho;
+    const real irho = qdiv(real(1), rho);
     const real ux = mx * irho, uy = my * irho, uz = mz * irho;
     const real uu = ux * ux + uy * uy + uz * uz;
     const real cY0 = rY * irho, cB0 = rB * irho;
@@ -571,7 +594,7 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     }
     const real Fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
     const real gN2 = gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2];
-    const real gNn = rsqrt_(gN2);
+    const real gNn = qsqrt(gN2);
 
     // non-equilibrium stresses (Eq. 20): ink Pi^Y = sum f^Y c c - rY (pfac_Y I + u u),
     // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
@@ -636,13 +659,13 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
 
     // local relaxation time: ink viscosity from Eq. 24-25, harmonic mixing
     // by mass fraction (Eq. 17), clamp
-    const real S = rsqrt_(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
+    const real S = qsqrt(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
                           real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
     const real tauY = solve_tau_ink(p, S, rY, rho);
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
-    const real inv_nu = cY0 / nuY + cB0 / p.nuB;
-    const real tau = clampr(real(0.5) + real(3) / inv_nu, p.tau_min, p.tau_max);
-    const real om45 = (real(1) - real(1) / tau) * real(4.5);
+    const real inv_nu = qdiv(cY0, nuY) + qdiv(cB0, p.nuB);
+    const real tau = clampr(real(0.5) + qdiv(real(3), inv_nu), p.tau_min, p.tau_max);
+    const real om45 = (real(1) - qdiv(real(1), tau)) * real(4.5);
 
     // body force and drag by the exact difference method (Eq. 29): the
     // equilibrium is taken at v = u + F/rho, f^eq(u) + [f^eq(v) - f^eq(u)]
@@ -659,8 +682,8 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     // cos(phi_i) regularised as c.grad / (|c| sqrt(|grad|^2 + eps^2)), eps = 1e-4
     const bool pert = gNn > real(0) && Fn2 > real(0);
     const real pA = pert ? real(0.5) * p.A * gNn : real(0);
-    const real pAF = pert ? pA / Fn2 : real(0);
-    const real rec = p.beta * rY * rB * irho * irho / rsqrt_(gN2 + real(1e-8));
+    const real pAF = pert ? qdiv(pA, Fn2) : real(0);
+    const real rec = p.beta * rY * rB * irho * irho * qrsqrt(gN2 + real(1e-8));
     const real tr3 = (PT[0] + PT[1] + PT[2]) * real(1.0 / 3.0);
     const real drho = rho - p.rho_ref;
 

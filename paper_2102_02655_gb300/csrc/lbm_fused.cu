@@ -157,12 +157,11 @@ struct Colour {
     static constexpr int NV = kUnit ? 1 : 3;
     real* col;  // [3 slots][NV][HS]
     __device__ __forceinline__ void put(const StepArgs<real>& p, int slot, int j, real rY, real rB) const {
-        const real inv = real(1) / (rY + rB);
         if constexpr (kUnit) {
-            col[slot * HS + j] = rY * inv;
+            col[slot * HS + j] = colour_frac(rY, rB);
         } else {
-            col[(slot * 3 + 0) * HS + j] = rY * inv;
-            col[(slot * 3 + 1) * HS + j] = rB * inv;
+            col[(slot * 3 + 0) * HS + j] = colour_frac(rY, rB);
+            col[(slot * 3 + 1) * HS + j] = colour_frac(rB, rY);
             col[(slot * 3 + 2) * HS + j] = phase_field(p, rY, rB);
         }
     }
@@ -286,6 +285,30 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
         }
     };
 
+    // Plane zz below the top (1 <= zz <= nz - 2) for the own site (kept in
+    // buffer zz & 1) and the halo site: both pulls are issued before either
+    // is consumed, so the halo threads wait for one memory round trip, not two.
+    const bool has_halo = tid < NRING;
+    int rx = 0, ry = 0;
+    if (has_halo) ring_coord<HX, HY>(tid, &rx, &ry);
+    const int hgx = wrapn(x0 - 1 + rx, p.nx), hgy = wrapn(y0 - 1 + ry, p.ny);
+    const int hj = ry * HX + rx;
+    auto load_interior = [&](int zz) {
+        real f[2][19], h[2][19];
+        pull_interior(p, gx, gy, zz, f);
+        if (has_halo) pull_interior(p, hgx, hgy, zz, h);
+        real* b = pops + (zz & 1) * 38 * NT + tid;
+#pragma unroll
+        for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
+        real rY, rB;
+        density(f, p, &rY, &rB);
+        C.put(p, slot_of(zz), hidx, rY, rB);
+        if (has_halo) {
+            density(h, p, &rY, &rB);
+            C.put(p, slot_of(zz), hj, rY, rB);
+        }
+    };
+
     // prologue: planes za - 1 and za
     if (za == 0) {
         // plane 0 with two rings, for the substrate ghost plane z = -1 built by
@@ -320,7 +343,8 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
         // (z + 1) & 1: no collision still running (plane z - 1, other threads)
         // reads that slot, and the buffer's previous plane was read by this
         // thread only
-        if (z + 1 < p.nz) load_plane(z + 1, true, false);
+        if (z + 1 < p.nz - 1) load_interior(z + 1);
+        else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
             real f[2][19];

@@ -210,7 +210,7 @@ struct ArrayNbUnit {
         if (p->z_mode == kZPeriodic) z1 = wrapn(z1, p->nz);
         const long long r1 = ridx(*p, x1, y1, z1);
         const real a = p->rho_cur[r1], b = p->rho_cur[comp + r1];
-        return a / (a + b);
+        return colour_frac(a, b);
     }
 };
 
@@ -225,9 +225,8 @@ struct ArrayNb {
         if (p->z_mode == kZPeriodic) z1 = wrapn(z1, p->nz);
         const long long r1 = ridx(*p, x1, y1, z1);
         const real a = p->rho_cur[r1], b = p->rho_cur[comp + r1];
-        const real tot = a + b;
-        *cY = a / tot;
-        *cB = b / tot;
+        *cY = colour_frac(a, b);
+        *cB = colour_frac(b, a);
         *rn = phase_field(*p, a, b);
     }
 };
