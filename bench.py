@@ -28,7 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "2-component MLUPS & %HBM roofline; sweep sims/h, p50/p99 vs plain at same err"
 WORKLOAD = "print_512x128x128"
 REF_SAMPLE = "print_128x64x64"
-BYTES_PER_SITE = {"f32": 2 * 19 * 2 * 4, "f64": 2 * 19 * 2 * 8}  # read + write of the populations
+# read + write of the populations; 16-bit storage adds the FP32 ink fraction
+# per site (read and written once per site)
+BYTES_PER_SITE = {"f32": 2 * 19 * 2 * 4, "f64": 2 * 19 * 2 * 8, "f16dev": 2 * 19 * 2 * 2 + 8,
+                  "bf16dev": 2 * 19 * 2 * 2 + 8}
 
 
 def _peaks():
@@ -203,6 +206,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     wl = I.workload(args.workload)
+    if args.storage:
+        wl["params"]["storage"] = args.storage
     shape = wl["shape"]
     nsites = shape[0] * shape[1] * shape[2]
     storage = wl["params"]["storage"]
@@ -259,7 +264,7 @@ def run_ours(args):
 
     # end to end through the C ABI with pinned host buffers: upload the
     # initial fields, K steps, read back densities, velocity and diagnostics
-    esz = 4 if storage == "f32" else 8
+    esz = 8 if storage == "f64" else 4
     e2e, unstable = None, 0
     if not args.no_e2e:
         e2e, unstable = run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws)
@@ -275,11 +280,11 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
-                "config": {"workload": args.workload, "lattice": "D3Q19", "sites": nsites,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "lattice": "D3Q19", "sites": nsites, "storage": storage,
                            "path": "fused bulk kernel + phase-by-phase nozzle box",
                            "nozzle": "r 10, gap 20, head 0.01 l.u./step, power-law n 0.6, extrusion 0.02",
-                           "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * nsites * esz * 2 / 1e9),
+                           "l2": "inputs larger than L2 (populations %.2f GB)" % (BYTES_PER_SITE[storage] * nsites / 1e9),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "unstable": unstable}
@@ -292,8 +297,8 @@ def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
     import numpy as np
     import torch
     from paper_2102_02655_gb300 import lbm
-    npd = np.float32 if storage == "f32" else np.float64
-    tdt = torch.float32 if storage == "f32" else torch.float64
+    npd = np.float64 if storage == "f64" else np.float32
+    tdt = torch.float64 if storage == "f64" else torch.float32
     h_rY = torch.from_numpy(rY.astype(npd)).pin_memory()
     h_rB = torch.from_numpy(rB.astype(npd)).pin_memory()
     outs = [torch.empty(rY.shape, dtype=tdt).pin_memory() for _ in range(5)]
@@ -305,7 +310,7 @@ def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
     res = lat.fields(mask=lbm.LBM_FIELD_RHO_INK | lbm.LBM_FIELD_RHO_AMB | lbm.LBM_FIELD_U,
                      out=[o.numpy() for o in outs])
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    esz = 4 if storage == "f32" else 8
+    esz = 8 if storage == "f64" else 4
     e2e = {"value": aggregate_mlups(ws, nsites, args.steps, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": 2 * nsites * esz / args.steps,
            "d2h_bytes_per_step": (5 * nsites * esz + 120) / args.steps,
@@ -322,6 +327,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", choices=["f64", "f32", "f16dev", "bf16dev"], default=None,
+                    help="population storage (default: the workload's, FP32)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="throughput workload (default: the 512x128x128 print lattice)")
     args = ap.parse_args()

@@ -17,7 +17,7 @@
  *    handle refuses further work and must be destroyed.
  *  - Pointers named *_dev or passed with on_device = 1 are device pointers on
  *    the handle's device; others are host pointers. Field values are double
- *    for LBM_F64 storage and float otherwise.
+ *    for LBM_F64 storage and float otherwise (F32, F16DEV, BF16DEV).
  *  - Calls on one handle must not overlap (one host thread at a time).
  */
 #ifndef LBM_H
@@ -43,8 +43,15 @@ typedef enum {
  * plane (ny must be 1); D3Q19 is the standard 3D set used for 3D lattices. */
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_velset;
 
-/* Storage and arithmetic precision of the populations. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1 } lbm_storage;
+/* Storage of the populations. F64 and F32 store and compute in that type.
+ * F16DEV and BF16DEV store 16-bit deviations from a local rest state and
+ * compute in FP32 (reductions in FP64): slot 1 holds the total deviation
+ * f^Y_i + f^B_i - w_i rho0_amb, slot 0 the ink population minus
+ * c w_i rho0_amb, c the ink fraction of the site that wrote it (kept per site
+ * in FP32 beside each population buffer). 2 x Q x 2 bytes + 4 bytes per site
+ * and buffer instead of 2 x Q x 4. Fields and diagnostics are FP32/FP64 as for
+ * F32. Not accepted by lbm_step_noalloc. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16DEV = 2, LBM_BF16DEV = 3 } lbm_storage;
 
 /* Execution path: PLAIN runs the phase-by-phase kernels over the whole
  * lattice; FUSED runs the fused z-marching kernel over the bulk and the

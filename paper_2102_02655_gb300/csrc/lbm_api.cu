@@ -53,7 +53,9 @@ struct lbm_handle {
     cudaEvent_t fork = nullptr, join = nullptr;
     int Q = 19;
     long long N = 0, plane = 0;
-    size_t esize = 8;  // bytes per real
+    size_t esize = 8;  // bytes per real (compute type)
+    size_t psize = 8;  // bytes per stored population
+    size_t fdata = 0;  // bytes of populations in a buffer; 16-bit storage keeps the ink-fraction array after them
     // device buffers
     void* f[2] = {nullptr, nullptr};
     void* rho[2] = {nullptr, nullptr};
@@ -205,8 +207,12 @@ void fill_geometry(const lbm_handle* h, StepArgs<real>& p, long long n) {
 template <typename real>
 void fill_buffers(lbm_handle* h, StepArgs<real>& p, int src) {
     const int dst = 1 - src;
-    p.fin = (const real*)h->f[src];
-    p.fout = (real*)h->f[dst];
+    p.fin = h->f[src];
+    p.fout = h->f[dst];
+    if (h->psize == 2) {
+        p.ref_in = (const real*)((const char*)h->f[src] + h->fdata);
+        p.ref_out = (real*)((char*)h->f[dst] + h->fdata);
+    }
     p.rho_prev = (const real*)h->rho[src];
     p.rho_cur = (real*)h->rho[dst];
     p.u_prev = (const real*)h->u[src];
@@ -302,7 +308,7 @@ lbm_status mark(lbm_handle* h, int g, bool end, long long sites, cudaStream_t st
     return LBM_OK;
 }
 
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 lbm_status do_steps(lbm_handle* h, int nsteps) {
     for (int t = 0; t < nsteps; ++t) {
         StepArgs<real> p;
@@ -328,12 +334,12 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork, 0);
                 if (e != cudaSuccess) return cuda_check(h, e, "fork");
                 if ((st = mark(h, 1, false, 0, h->side)) != LBM_OK) return st;
-                launched += launch_plain<VS, real>(p, box, grow(box, 1, nx, ny, nz), grow(box, 2, nx, ny, nz),
-                                                   h->side);
+                launched += launch_plain<VS, real, S>(p, box, grow(box, 1, nx, ny, nz), grow(box, 2, nx, ny, nz),
+                                                      h->side);
                 if ((st = mark(h, 1, true, box_sites, h->side)) != LBM_OK) return st;
             }
             if ((st = mark(h, 0, false, 0, h->stream)) != LBM_OK) return st;
-            launched += launch_fused<real>(p, h->zchunk, h->stream, h->variant);
+            launched += launch_fused<real, S>(p, h->zchunk, h->stream, h->variant);
             if ((st = mark(h, 0, true, h->N - box_sites, h->stream)) != LBM_OK) return st;
             if (box.wx > 0) {
                 cudaError_t e = cudaEventRecord(h->join, h->side);
@@ -343,7 +349,7 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
         } else {
             const Region R = full_region(h);
             if ((st = mark(h, 1, false, 0, h->stream)) != LBM_OK) return st;
-            launched += launch_plain<VS, real>(p, R, R, R, h->stream);
+            launched += launch_plain<VS, real, S>(p, R, R, R, h->stream);
             if ((st = mark(h, 1, true, h->N, h->stream)) != LBM_OK) return st;
         }
         h->launches += launched;
@@ -355,7 +361,7 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
     return LBM_OK;
 }
 
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 lbm_status do_init(lbm_handle* h, int staged, int have_u) {
     StepArgs<real> p;
     memset(&p, 0, sizeof(p));
@@ -365,18 +371,25 @@ lbm_status do_init(lbm_handle* h, int staged, int have_u) {
     cudaError_t e = cudaMemsetAsync(h->acc, 0, kAccN * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaMemsetAsync");
-    h->launches += launch_init<VS, real>(p, staged, have_u, h->stream);
+    h->launches += launch_init<VS, real, S>(p, staged, have_u, h->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(h, e, "init launch");
     return LBM_OK;
 }
 
 lbm_status dispatch_init(lbm_handle* h, int staged, int have_u) {
-    if (h->cfg.velset == LBM_D3Q19)
-        return h->cfg.storage == LBM_F64 ? do_init<D3Q19, double>(h, staged, have_u)
-                                         : do_init<D3Q19, float>(h, staged, have_u);
-    return h->cfg.storage == LBM_F64 ? do_init<D2Q9, double>(h, staged, have_u)
-                                     : do_init<D2Q9, float>(h, staged, have_u);
+    const bool d3 = h->cfg.velset == LBM_D3Q19;
+    switch (h->cfg.storage) {
+    case LBM_F64:
+        return d3 ? do_init<D3Q19, double, double>(h, staged, have_u) : do_init<D2Q9, double, double>(h, staged, have_u);
+    case LBM_F16DEV:
+        return d3 ? do_init<D3Q19, float, __half>(h, staged, have_u) : do_init<D2Q9, float, __half>(h, staged, have_u);
+    case LBM_BF16DEV:
+        return d3 ? do_init<D3Q19, float, __nv_bfloat16>(h, staged, have_u)
+                  : do_init<D2Q9, float, __nv_bfloat16>(h, staged, have_u);
+    default:
+        return d3 ? do_init<D3Q19, float, float>(h, staged, have_u) : do_init<D2Q9, float, float>(h, staged, have_u);
+    }
 }
 
 lbm_status check_usable(lbm_handle* h) {
@@ -403,7 +416,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         return fail(nullptr, LBM_EINVAL, "lbm_create: unknown velocity set %d", cfg->velset);
     if (cfg->velset == LBM_D2Q9 && cfg->ny != 1)
         return fail(nullptr, LBM_EINVAL, "lbm_create: D2Q9 lattices lie in the x-z plane, ny must be 1");
-    if (cfg->storage != LBM_F64 && cfg->storage != LBM_F32)
+    if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16DEV)
         return fail(nullptr, LBM_EINVAL, "lbm_create: unknown storage %d", cfg->storage);
     if (cfg->path < LBM_PATH_AUTO || cfg->path > LBM_PATH_FUSED)
         return fail(nullptr, LBM_EINVAL, "lbm_create: unknown path %d", cfg->path);
@@ -431,6 +444,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->plane = (long long)cfg->nx * cfg->ny;
     h->N = h->plane * cfg->nz;
     h->esize = cfg->storage == LBM_F64 ? 8 : 4;
+    h->psize = cfg->storage == LBM_F64 ? 8 : (cfg->storage == LBM_F32 ? 4 : 2);
     {
         // z-planes per CTA of the fused kernel: about six waves of two CTAs
         // per SM (measured best on the 512x128x128 lattice: 16 planes), at
@@ -468,7 +482,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         lbm_destroy(h);
         return LBM_ECUDA;
     }
-    const size_t fbytes = (size_t)2 * h->Q * h->N * h->esize;
+    h->fdata = ((size_t)2 * h->Q * h->N * h->psize + 255) & ~(size_t)255;
+    const size_t fbytes = h->fdata + (h->psize == 2 ? (size_t)h->N * h->esize : 0);
     const size_t rbytes = (size_t)2 * (h->N + 2 * h->plane) * h->esize;
     const size_t ubytes = (size_t)3 * 2 * h->plane * h->esize;
     const size_t fldbytes = (size_t)kNFields * h->N * h->esize;
@@ -575,9 +590,14 @@ lbm_status lbm_step(lbm_handle* h, int nsteps) {
     if (!h->have_geom || !h->have_rheo) return fail(h, LBM_ESTATE, "lbm_step: geometry and rheology must be set");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "lbm_step: nsteps < 0");
     if (nsteps == 0) return LBM_OK;
-    if (h->cfg.velset == LBM_D3Q19)
-        return h->cfg.storage == LBM_F64 ? do_steps<D3Q19, double>(h, nsteps) : do_steps<D3Q19, float>(h, nsteps);
-    return h->cfg.storage == LBM_F64 ? do_steps<D2Q9, double>(h, nsteps) : do_steps<D2Q9, float>(h, nsteps);
+    const bool d3 = h->cfg.velset == LBM_D3Q19;
+    switch (h->cfg.storage) {
+    case LBM_F64: return d3 ? do_steps<D3Q19, double, double>(h, nsteps) : do_steps<D2Q9, double, double>(h, nsteps);
+    case LBM_F16DEV: return d3 ? do_steps<D3Q19, float, __half>(h, nsteps) : do_steps<D2Q9, float, __half>(h, nsteps);
+    case LBM_BF16DEV:
+        return d3 ? do_steps<D3Q19, float, __nv_bfloat16>(h, nsteps) : do_steps<D2Q9, float, __nv_bfloat16>(h, nsteps);
+    default: return d3 ? do_steps<D3Q19, float, float>(h, nsteps) : do_steps<D2Q9, float, float>(h, nsteps);
+    }
 }
 
 lbm_status lbm_sync(lbm_handle* h, int timeout_ms) {
@@ -742,8 +762,8 @@ lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void*
     // velocity arrays are written before they are read
     cudaError_t e = cudaMemsetAsync(scratch, 0, 512, st);
     if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaMemsetAsync: %s", cudaGetErrorString(e));
-    p.fin = (const real*)f_in;
-    p.fout = (real*)f_out;
+    p.fin = f_in;
+    p.fout = f_out;
     p.rho_prev = rho_prev;
     p.rho_cur = rho_cur;
     p.u_prev = u_prev;
@@ -755,7 +775,7 @@ lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void*
     p.box = Region{0, 0, 0, 0, 0, 0};
     launch_prev_from_f<VS, real>(p, rho_prev, u_prev, st);
     const Region R = full_region(tmp);
-    launch_plain<VS, real>(p, R, R, R, st);
+    launch_plain<VS, real, real>(p, R, R, R, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: launch: %s", cudaGetErrorString(e));
     if (!diag) return LBM_OK;

@@ -13,6 +13,10 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace cglbm {
@@ -136,9 +140,11 @@ struct StepArgs {
     int unit;          // rho0_ink == rho0_amb and phi = w for both (density ratio one)
     int law, max_iter;
     real nu0, nu_inf, lambda, n_exp, K, tau_min, tau_max, tol;
-    // state
-    const real* fin;
-    real* fout;
+    // state: populations in the stored type S of the kernels (see Stored)
+    const void* fin;
+    void* fout;
+    const real* ref_in;    // 16-bit storage: ink fraction of each site of fin
+    real* ref_out;         // and of fout
     real* rho_cur;         // (nz + 2) planes, z = -1 .. nz
     const real* rho_prev;
     const real* u_prev;    // physical velocity of the last two planes, 3 x 2 x plane
@@ -153,6 +159,75 @@ struct StepArgs {
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
+
+// Population storage. S is the stored type: the compute type itself (FP64 or
+// FP32), or a 16-bit type (FP16, BF16) that holds deviations from a local
+// rest state, so that its 11 or 8 significant bits resolve the dynamics
+// rather than the rest populations. Slot 1 holds the total deviation
+// d_i = f^Y_i + f^B_i - w_i rho_ref in every case. With 16-bit storage slot 0
+// holds f^Y_i - c w_i rho_ref, c the ink fraction rho_Y / rho of the site
+// that wrote the value; c is kept per site (compute type) beside each
+// population buffer, so a pull from x - c_i adds back c(x - c_i) w_i rho_ref.
+template <typename S>
+struct Stored {
+    static constexpr bool kDev = false;
+};
+template <>
+struct Stored<__half> {
+    static constexpr bool kDev = true;
+};
+template <>
+struct Stored<__nv_bfloat16> {
+    static constexpr bool kDev = true;
+};
+
+template <typename S, typename real, typename Idx>
+__device__ __forceinline__ real s_get(const void* b, Idx k) {
+    if constexpr (std::is_same<S, __half>::value) return __half2float(static_cast<const __half*>(b)[k]);
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(b)[k]);
+    else return static_cast<const real*>(b)[k];
+}
+
+template <typename S, typename real, typename Idx>
+__device__ __forceinline__ void s_put(void* b, Idx k, real v) {
+    if constexpr (std::is_same<S, __half>::value) static_cast<__half*>(b)[k] = __float2half_rn(v);
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+        static_cast<__nv_bfloat16*>(b)[k] = __float2bfloat16_rn(v);
+    else static_cast<real*>(b)[k] = v;
+}
+
+// Both slots of direction i written at site s (of N) into buffer b with
+// ink-fraction array ref: the post-collision populations of step n-1 when
+// b = fin, or this step's values at s when b = fout (in place).
+template <class VS, typename S, typename real, typename Idx>
+__device__ __forceinline__ void pop_get(const StepArgs<real>& p, const void* b, const real* ref, int i, Idx s, Idx N,
+                                        real* fY, real* fD) {
+    *fY = s_get<S, real>(b, (Idx)i * N + s);
+    *fD = s_get<S, real>(b, (Idx)(VS::Q + i) * N + s);
+    if constexpr (Stored<S>::kDev) *fY += (real)VS::w(i) * p.rho_ref * ref[s];
+}
+
+// Store both slots of direction i at site s of fout; c is the site's ink
+// fraction (written once per site with ref_put).
+template <class VS, typename S, typename real, typename Idx>
+__device__ __forceinline__ void pop_put(const StepArgs<real>& p, int i, Idx s, Idx N, real fY, real fD, real c) {
+    if constexpr (Stored<S>::kDev) fY -= (real)VS::w(i) * p.rho_ref * c;
+    s_put<S, real>(p.fout, (Idx)i * N + s, fY);
+    s_put<S, real>(p.fout, (Idx)(VS::Q + i) * N + s, fD);
+}
+
+template <typename S, typename real, typename Idx>
+__device__ __forceinline__ void ref_put(const StepArgs<real>& p, Idx s, real c) {
+    if constexpr (Stored<S>::kDev) p.ref_out[s] = c;
+}
+
+// ink fraction used as the 16-bit reference (0 for an empty site)
+template <typename real>
+__device__ __forceinline__ real ref_frac(real rY, real rB) {
+    const real t = rY + rB;
+    return t > real(0) ? rY / t : real(0);
+}
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 // periodic wrap of any offset; the modulo runs only when a leaves [0, n)
@@ -301,7 +376,7 @@ __device__ __forceinline__ bool clear_of_nozzle(const StepArgs<real>& p, int x, 
     return d2 < p.rclear_in2 || d2 > p.rclear_out2;
 }
 
-template <class VS, typename real>
+template <class VS, typename S, typename real>
 __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int y, int z, real f[2][VS::Q],
                                              real bc[2]) {
     const long long s = sidx(p, x, y, z);
@@ -317,14 +392,11 @@ __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int
             long long src;
             if (p.z_mode == kZPeriodic) sz = wrapn(sz, p.nz);
             if (sz < 0) {
-                src = s;
-                f[0][i] = p.fin[(long long)opp(i) * p.N + src];
-                f[1][i] = p.fin[(long long)(VS::Q + opp(i)) * p.N + src];
+                pop_get<VS, S>(p, p.fin, p.ref_in, opp(i), s, p.N, &f[0][i], &f[1][i]);
                 continue;
             }
             src = sidx(p, cx > 0 ? xm : (cx < 0 ? xp : x), cy > 0 ? ym : (cy < 0 ? yp : y), sz);
-            f[0][i] = p.fin[(long long)i * p.N + src];
-            f[1][i] = p.fin[(long long)(VS::Q + i) * p.N + src];
+            pop_get<VS, S>(p, p.fin, p.ref_in, i, src, p.N, &f[0][i], &f[1][i]);
         }
         return;
     }
@@ -338,12 +410,11 @@ __device__ __forceinline__ void pull_general(const StepArgs<real>& p, int x, int
         const int kind = classify(p, x, y, z, cx, cy, cz, &src, uw);
         const int ib = opp(i);
         if (kind == kLinkFluid) {
-            f[0][i] = p.fin[(long long)i * p.N + src];
-            f[1][i] = p.fin[(long long)(VS::Q + i) * p.N + src];
+            pop_get<VS, S>(p, p.fin, p.ref_in, i, src, p.N, &f[0][i], &f[1][i]);
             continue;
         }
-        const real oY = p.fin[(long long)ib * p.N + s];            // f*^Y_ib(x), heading to the boundary
-        const real oD = p.fin[(long long)(VS::Q + ib) * p.N + s];  // d*_ib(x)
+        real oY, oD;  // f*^Y_ib(x) and d*_ib(x), heading to the boundary
+        pop_get<VS, S>(p, p.fin, p.ref_in, ib, s, p.N, &oY, &oD);
         const real w = (real)VS::w(ib);
         real vY, vD;
         if (kind == kLinkRest) {
@@ -496,6 +567,7 @@ __device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, r
 template <typename real>
 struct SiteOut {
     real rhoY, rhoB, u[3], tau, rn;
+    real cY;  // ink fraction rho_Y / rho after streaming
 };
 
 template <typename real>
@@ -730,6 +802,7 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     so->u[2] = uz + real(0.5) * Fb[2] * irho;
     so->tau = tau;
     so->rn = rn0;
+    so->cY = cY0;
 }
 
 // unstable: the total density is not finite and positive (a vanishing

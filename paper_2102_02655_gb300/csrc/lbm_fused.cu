@@ -40,7 +40,7 @@ __device__ __forceinline__ int slot_of(int z) { return (z + 4) & 3; }  // z >= -
 // substrate, where the resting half-way wall bounces the population back
 // (the pull then reads the opposite direction at the site itself). Branch-free:
 // the substrate case is an address select on the upward directions only.
-template <typename real>
+template <typename S, typename real>
 __device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19]) {
     using VS = D3Q19;
     const int nx = p.nx, ny = p.ny, pl = (int)p.plane, N = (int)p.N;
@@ -49,16 +49,20 @@ __device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, i
     const int rm = (gy == 0 ? ny - 1 : gy - 1) * nx, rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
     const int s = zz * pl + r0 + gx;
     const bool bottom = zz == 0;
-    const real* fin = p.fin;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
         const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
         const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
-        int idx = i * N + zz * pl - cz * pl + sy + sx;
-        if (cz > 0) idx = bottom ? opp(i) * N + s : idx;
-        f[0][i] = fin[idx];
-        f[1][i] = fin[idx + 19 * N];
+        int src = zz * pl - cz * pl + sy + sx;
+        int idx = i * N + src;
+        if (cz > 0) {
+            idx = bottom ? opp(i) * N + s : idx;
+            src = bottom ? s : src;
+        }
+        f[0][i] = s_get<S, real>(p.fin, idx);
+        f[1][i] = s_get<S, real>(p.fin, idx + 19 * N);
+        if constexpr (Stored<S>::kDev) f[0][i] += (real)VS::w(i) * p.rho_ref * p.ref_in[src];
     }
 }
 
@@ -76,7 +80,7 @@ struct TopPull {
     real rY, rB;
     double b0, b1;
 };
-template <typename real>
+template <typename S, typename real>
 __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int gx, int gy, real* dst, int stride,
                                                   bool ledger) {
     using VS = D3Q19;
@@ -87,7 +91,6 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
     const int rm = (gy == 0 ? ny - 1 : gy - 1) * nx, rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
     const int zoff = zz * pl;
     const int s = zoff + r0 + gx;
-    const real* fin = p.fin;
     TopPull<real> r{real(0), real(0), 0.0, 0.0};
     real sumD = 0;
 #pragma unroll 1
@@ -97,8 +100,7 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
         const int ib = opp(i);
         real fY, fD;
         if (sz < 0) {
-            fY = fin[ib * N + s];
-            fD = fin[(19 + ib) * N + s];
+            pop_get<VS, S>(p, p.fin, p.ref_in, ib, s, N, &fY, &fD);
         } else if (sz >= p.nz) {
             real uw[3];
             const int x1 = cx > 0 ? xp : (cx < 0 ? xm : gx), y1 = cy > 0 ? rp : (cy < 0 ? rm : r0);
@@ -109,8 +111,8 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
             const real cu = -(real)(cx * uw[0] + cy * uw[1] + cz * uw[2]);  // c_ib . u_w
             const real q = real(4.5) * cu * cu - real(1.5) * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
             const real w = (real)(VS::w(1) * (i <= 6) + VS::w(7) * (i > 6));
-            const real oY = fin[ib * N + s];
-            const real oD = fin[(19 + ib) * N + s];
+            real oY, oD;
+            pop_get<VS, S>(p, p.fin, p.ref_in, ib, s, N, &oY, &oD);
             fY = -oY;  // imposed ink density 0
             fD = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
             if (ledger) {
@@ -121,8 +123,7 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
             const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
             const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
             const int src = zoff - cz * pl + sy + sx;
-            fY = fin[i * N + src];
-            fD = fin[(19 + i) * N + src];
+            pop_get<VS, S>(p, p.fin, p.ref_in, i, src, N, &fY, &fD);
         }
         if (dst) {
             dst[i * stride] = fY;
@@ -209,7 +210,7 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 
 // The own sites' pulled populations wait in shared memory for their
 // collision (one plane later); each thread reads back only its own column.
-template <typename real, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB>
 __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     using T = Tile<TY_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
@@ -263,14 +264,14 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
             real rY, rB;
             if (zz == p.nz - 1) {
                 const TopPull<real> r =
-                    pull_top(p, px, py, dst, NT, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
+                    pull_top<S>(p, px, py, dst, NT, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
                 rY = r.rY;
                 rB = r.rB;
                 bc[0] += r.b0;
                 bc[1] += r.b1;
             } else {
                 real f[2][19];
-                pull_interior(p, px, py, zz, f);
+                pull_interior<S>(p, px, py, zz, f);
                 if (dst) {
 #pragma unroll
                     for (int i = 0; i < 38; ++i) dst[i * NT] = f[i / 19][i % 19];
@@ -295,8 +296,8 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
     const int hj = ry * HX + rx;
     auto load_interior = [&](int zz) {
         real f[2][19], h[2][19];
-        pull_interior(p, gx, gy, zz, f);
-        if (has_halo) pull_interior(p, hgx, hgy, zz, h);
+        pull_interior<S>(p, gx, gy, zz, f);
+        if (has_halo) pull_interior<S>(p, hgx, hgy, zz, h);
         real* b = pops + (zz & 1) * 38 * NT + tid;
 #pragma unroll
         for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
@@ -361,10 +362,8 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
             const int s = z * (int)p.plane + y * p.nx + x;
             const int N = (int)p.N;
 #pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                p.fout[i * N + s] = f[0][i];
-                p.fout[(19 + i) * N + s] = f[1][i];
-            }
+            for (int i = 0; i < 19; ++i) pop_put<D3Q19, S>(p, i, s, N, f[0][i], f[1][i], so.cY);
+            ref_put<S>(p, s, so.cY);
             if (z >= p.nz - 2)
                 for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
             if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
@@ -406,7 +405,7 @@ constexpr size_t fused_smem() {
     return sizeof(real) * (2 * 38 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     using T = Tile<TY_>;
     constexpr size_t smem = fused_smem<real, kUnit, TY_>();
@@ -415,37 +414,40 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, kUnit, TY_, MINB><<<grid, block, smem, st>>>(p, zchunk);
+    k_fused<real, S, kUnit, TY_, MINB><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
-template <typename real, int TY_, int MINB>
+template <typename real, typename S, int TY_, int MINB>
 int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, true, TY_, MINB>(p, zchunk, st)
-                  : launch_one<real, false, TY_, MINB>(p, zchunk, st);
+    return p.unit ? launch_one<real, S, true, TY_, MINB>(p, zchunk, st)
+                  : launch_one<real, S, false, TY_, MINB>(p, zchunk, st);
 }
 
 }  // namespace
 
 // Variant 0 (default): 32 x 8 tiles, two CTAs per SM (one in FP64). Variant 1
 // (tuning measurements, CGLBM_FUSED_VARIANT=1): 32 x 16 tiles, one CTA per SM.
-template <typename real>
+template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
         (void)variant;
-        return launch_variant<real, 8, 1>(p, zchunk, st);
+        return launch_variant<real, S, 8, 1>(p, zchunk, st);
     } else {
-        if (variant == 1) return launch_variant<real, 16, 1>(p, zchunk, st);
-        return launch_variant<real, 8, 2>(p, zchunk, st);
+        if (variant == 1) return launch_variant<real, S, 16, 1>(p, zchunk, st);
+        return launch_variant<real, S, 8, 2>(p, zchunk, st);
     }
 }
 
-template int launch_fused<float>(const StepArgs<float>&, int, cudaStream_t, int);
-template int launch_fused<double>(const StepArgs<double>&, int, cudaStream_t, int);
+template int launch_fused<float, float>(const StepArgs<float>&, int, cudaStream_t, int);
+template int launch_fused<double, double>(const StepArgs<double>&, int, cudaStream_t, int);
+template int launch_fused<float, __half>(const StepArgs<float>&, int, cudaStream_t, int);
+template int launch_fused<float, __nv_bfloat16>(const StepArgs<float>&, int, cudaStream_t, int);
 
 }  // namespace cglbm

@@ -55,7 +55,7 @@ inline dim3 region_grid(const Region& r) {
 }
 
 // 1. stream + densities (post-streaming) of every fluid node of step n-1 in R2
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 __global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p, Region R2, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double bc0 = 0, bc1 = 0, de0 = 0, de1 = 0;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p
     if (region_site(R2, p.nx, p.ny, &x, &y, &z) && !solid_at(p, x, y, z, 0)) {
         real f[2][VS::Q];
         real bc[2] = {real(0), real(0)};
-        pull_general<VS>(p, x, y, z, f, bc);
+        pull_general<VS, S>(p, x, y, z, f, bc);
         real rY = 0, sd = 0;
 #pragma unroll
         for (int i = 0; i < VS::Q; ++i) { rY += f[0][i]; sd += f[1][i]; }
@@ -80,11 +80,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p
             } else {
                 // the collision of this site reads these in place (step 4)
                 const long long s = sidx(p, x, y, z);
+                const real c = ref_frac(rY, rB);
 #pragma unroll
-                for (int i = 0; i < VS::Q; ++i) {
-                    p.fout[(long long)i * p.N + s] = f[0][i];
-                    p.fout[(long long)(VS::Q + i) * p.N + s] = f[1][i];
-                }
+                for (int i = 0; i < VS::Q; ++i) pop_put<VS, S>(p, i, s, p.N, f[0][i], f[1][i], c);
+                ref_put<S>(p, s, c);
             }
         }
     }
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p
 
 // 2. nodes the nozzle uncovered: mean density of the neighbours that are fluid
 //    at both steps (Sec. II B)
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 __global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R1, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double c0 = 0, c1 = 0;
@@ -128,13 +127,14 @@ __global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R
             // populations of the created node: equilibrium at the nozzle velocity
             const long long s = sidx(p, x, y, z);
             const real uu = p.vn[0] * p.vn[0] + p.vn[1] * p.vn[1] + p.vn[2] * p.vn[2];
+            const real c = ref_frac(m0, m1);
 #pragma unroll
             for (int i = 0; i < VS::Q; ++i) {
                 real eY, eD;
                 feq_pair<VS>(p, i, m0, m1, p.vn[0], p.vn[1], p.vn[2], uu, &eY, &eD);
-                p.fout[(long long)i * p.N + s] = eY;
-                p.fout[(long long)(VS::Q + i) * p.N + s] = eD;
+                pop_put<VS, S>(p, i, s, p.N, eY, eD, c);
             }
+            ref_put<S>(p, s, c);
         }
     }
     warp_add(p.acc + kAccCreated, c0);
@@ -248,7 +248,7 @@ __device__ __forceinline__ void store_fields(const StepArgs<real>& p, long long 
 
 // 4. collision at every fluid node of step n in R, in place: steps 1 and 2
 //    left the post-streaming (or created) populations in fout
-template <class VS, typename real, bool kUnit>
+template <class VS, typename real, bool kUnit, typename S>
 __global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Region R) {
     const long long comp = p.N + 2 * p.plane;
     double m0 = 0, m1 = 0, px = 0, py = 0, pz = 0;
@@ -264,10 +264,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Regio
     } else if (active) {
         real f[2][VS::Q];
 #pragma unroll
-        for (int i = 0; i < VS::Q; ++i) {
-            f[0][i] = p.fout[(long long)i * p.N + s];
-            f[1][i] = p.fout[(long long)(VS::Q + i) * p.N + s];
-        }
+        for (int i = 0; i < VS::Q; ++i) pop_get<VS, S>(p, p.fout, p.ref_out, i, s, p.N, &f[0][i], &f[1][i]);
         SiteOut<real> so;
         const real zd = p.z_mode == kZWalls ? real(z) + real(0.5) : real(-1);
         if constexpr (kUnit) {
@@ -278,10 +275,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Regio
             collide<VS, real, false>(p, f, nb, zd, &so);
         }
 #pragma unroll
-        for (int i = 0; i < VS::Q; ++i) {
-            p.fout[(long long)i * p.N + s] = f[0][i];
-            p.fout[(long long)(VS::Q + i) * p.N + s] = f[1][i];
-        }
+        for (int i = 0; i < VS::Q; ++i) pop_put<VS, S>(p, i, s, p.N, f[0][i], f[1][i], so.cY);
+        ref_put<S>(p, s, so.cY);
         if (z >= p.nz - 2)
             for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
         if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
@@ -306,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Regio
 }
 
 // initial equilibrium state
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 __global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged, int have_u) {
     const long long comp = p.N + 2 * p.plane;
     double m0 = 0, m1 = 0;
@@ -338,13 +333,14 @@ __global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged,
             rB = ink ? real(0) : p.rho0[1];
         }
         const real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const real c = ref_frac(rY, rB);
 #pragma unroll
         for (int i = 0; i < VS::Q; ++i) {
             real eY, eD;
             feq_pair<VS>(p, i, rY, rB, u[0], u[1], u[2], uu, &eY, &eD);
-            p.fout[(long long)i * p.N + s] = eY;
-            p.fout[(long long)(VS::Q + i) * p.N + s] = eD;
+            pop_put<VS, S>(p, i, s, p.N, eY, eD, c);
         }
+        ref_put<S>(p, s, c);
         p.rho_cur[r] = rY;
         p.rho_cur[comp + r] = rB;
         if (z >= p.nz - 2)
@@ -374,7 +370,8 @@ __global__ void __launch_bounds__(kThreads) k_prev_from_f(StepArgs<real> p, real
         real rY = 0, sd = 0, m[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < VS::Q; ++i) {
-            const real a = p.fin[(long long)i * p.N + s], d = p.fin[(long long)(VS::Q + i) * p.N + s];
+            real a, d;
+            pop_get<VS, real>(p, p.fin, p.ref_in, i, s, p.N, &a, &d);
             rY += a;
             sd += d;
 #pragma unroll
@@ -411,35 +408,51 @@ template int launch_prev_from_f<D3Q19, double>(const StepArgs<double>&, double*,
 template int launch_prev_from_f<D2Q9, float>(const StepArgs<float>&, float*, float*, cudaStream_t);
 template int launch_prev_from_f<D2Q9, double>(const StepArgs<double>&, double*, double*, cudaStream_t);
 
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st) {
     if (region_sites(R) == 0) return 0;
-    k_stream_density<VS, real><<<region_grid(R2), kThreads, 0, st>>>(p, R2, R);
-    k_created<VS, real><<<region_grid(R1), kThreads, 0, st>>>(p, R1, R);
+    k_stream_density<VS, real, S><<<region_grid(R2), kThreads, 0, st>>>(p, R2, R);
+    k_created<VS, real, S><<<region_grid(R1), kThreads, 0, st>>>(p, R1, R);
     Region R1g = R1;
     if (p.z_mode == kZWalls) {
         if (R1g.z0 <= 0) R1g.z0 = -1;
         if (R1g.z1 >= p.nz) R1g.z1 = p.nz + 1;
     }
     k_wall<VS, real><<<region_grid(R1g), kThreads, 0, st>>>(p, R1g);
-    if (p.unit) k_collide<VS, real, true><<<region_grid(R), kThreads, 0, st>>>(p, R);
-    else k_collide<VS, real, false><<<region_grid(R), kThreads, 0, st>>>(p, R);
+    if (p.unit) k_collide<VS, real, true, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
+    else k_collide<VS, real, false, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
     return 4;
 }
 
-template <class VS, typename real>
+template <class VS, typename real, typename S>
 int launch_init(const StepArgs<real>& p, int staged, int have_u, cudaStream_t st) {
-    k_init<VS, real><<<blocks_for(p.N), kThreads, 0, st>>>(p, staged, have_u);
+    k_init<VS, real, S><<<blocks_for(p.N), kThreads, 0, st>>>(p, staged, have_u);
     return 1;
 }
 
-template int launch_plain<D3Q19, float>(const StepArgs<float>&, const Region&, const Region&, const Region&, cudaStream_t);
-template int launch_plain<D3Q19, double>(const StepArgs<double>&, const Region&, const Region&, const Region&, cudaStream_t);
-template int launch_plain<D2Q9, float>(const StepArgs<float>&, const Region&, const Region&, const Region&, cudaStream_t);
-template int launch_plain<D2Q9, double>(const StepArgs<double>&, const Region&, const Region&, const Region&, cudaStream_t);
-template int launch_init<D3Q19, float>(const StepArgs<float>&, int, int, cudaStream_t);
-template int launch_init<D3Q19, double>(const StepArgs<double>&, int, int, cudaStream_t);
-template int launch_init<D2Q9, float>(const StepArgs<float>&, int, int, cudaStream_t);
-template int launch_init<D2Q9, double>(const StepArgs<double>&, int, int, cudaStream_t);
+template int launch_plain<D3Q19, float, float>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D3Q19, float, float>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_plain<D3Q19, double, double>(const StepArgs<double>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D3Q19, double, double>(const StepArgs<double>&, int, int, cudaStream_t);
+template int launch_plain<D3Q19, float, __half>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D3Q19, float, __half>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_plain<D3Q19, float, __nv_bfloat16>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D3Q19, float, __nv_bfloat16>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_plain<D2Q9, float, float>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D2Q9, float, float>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_plain<D2Q9, double, double>(const StepArgs<double>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D2Q9, double, double>(const StepArgs<double>&, int, int, cudaStream_t);
+template int launch_plain<D2Q9, float, __half>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D2Q9, float, __half>(const StepArgs<float>&, int, int, cudaStream_t);
+template int launch_plain<D2Q9, float, __nv_bfloat16>(const StepArgs<float>&, const Region&, const Region&, const Region&,
+                                               cudaStream_t);
+template int launch_init<D2Q9, float, __nv_bfloat16>(const StepArgs<float>&, int, int, cudaStream_t);
 
 }  // namespace cglbm

@@ -22,7 +22,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE",
                 5: "LBM_ETIMEOUT", 6: "LBM_ESTATE"}
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_F64, LBM_F32 = 0, 1
+LBM_F64, LBM_F32, LBM_F16DEV, LBM_BF16DEV = 0, 1, 2, 3
 LBM_PATH_AUTO, LBM_PATH_PLAIN, LBM_PATH_FUSED = 0, 1, 2
 LBM_Z_PERIODIC, LBM_Z_WALLS = 0, 1
 LBM_TOP_OPEN, LBM_TOP_WALL = 0, 1
@@ -195,7 +195,7 @@ def lbm_timings(h):
 # structs from dictionaries (same keys as the seeded workloads)
 # --------------------------------------------------------------------------
 
-_STORAGE = {"f64": LBM_F64, "f32": LBM_F32}
+_STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16dev": LBM_F16DEV, "bf16dev": LBM_BF16DEV}
 _PATH = {"auto": LBM_PATH_AUTO, "plain": LBM_PATH_PLAIN, "fused": LBM_PATH_FUSED}
 
 

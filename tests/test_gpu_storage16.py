@@ -1,0 +1,136 @@
+"""16-bit deviation storage (FP16 and BF16 populations, FP32 arithmetic, FP64
+reductions) against the FP64 oracle on the same seeded inputs.
+
+Bars. A stored population is rounded to 2^-11 (FP16) or 2^-8 (BF16) of its
+magnitude each step. The stored values are deviations from a local rest state
+(total deviation d_i; ink population minus c w_i rho_ref), of size up to
+~0.1 w_i in the print flow (the linear velocity term 3 w_i c_i.u and the
+recolouring term at the interface), so a step adds errors of ~1e-5 (FP16) and
+~1e-4 (BF16) to each population. They accumulate in the conserved moments and,
+through the velocity, in the interface position. Measured on the 64x32x32
+print run after 200 steps: FP16 <= 4.2e-4 on the hydrodynamic fields, BF16
+<= 1.3e-2 (the largest on uz, the extrusion direction), BF16/FP16 ~ 2^3 as the
+rounding units predict. The bars below are those levels with a margin of
+about 2.5; nu (a difference of O(1) moments, see the FP32 parity tests) and
+rho^N (twice the colour-fraction error) have their own bars.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_02655_gb300 import inputs as I
+
+from test_gpu_parity import _lbm, f32_exact, field_errors
+
+pytestmark = pytest.mark.gpu
+
+HYDRO = ("rho_ink", "rho_amb", "ux", "uy", "uz", "p")
+TOL16 = {"f16dev": 1e-3, "bf16dev": 3e-2}
+NU16 = {"f16dev": 6e-3, "bf16dev": 6e-2}
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "print_128x64x64_10k.npz")
+
+
+@pytest.fixture(scope="module")
+def small_print_200():
+    wl = I.workload("small_print_f64")
+    shape = wl["shape"]
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=0))
+    ref = O.Oracle(shape, params=wl["params"], geom=wl["geom"], rheo=wl["rheo"])
+    ref.set_fields(rY, rB)
+    ref.step(200)
+    return wl, (rY, rB), ref.fields(), ref.diag()
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_small_print_200_steps(small_print_200, storage, path):
+    lbm = _lbm()
+    wl, init, fo, do = small_print_200
+    lat = lbm.Lattice(wl["shape"], dict(wl["params"], storage=storage), wl["geom"], wl["rheo"], path=path)
+    lat.set_fields(*init)
+    lat.step(200)
+    fg = lat.fields()
+    lat.close()
+    assert fg["diag"]["unstable"] == 0
+    e = field_errors(fg, fo)
+    bad = {k: v for k, v in e.items() if k in HYDRO and not v <= TOL16[storage]}
+    assert not bad, "%s %s: %s" % (storage, path, bad)
+    assert e["nu"] <= NU16[storage], e
+    assert e["rhoN"] <= 2 * TOL16[storage], e
+    assert np.array_equal(np.asarray(fg["solid"]) != 0, np.asarray(fo["solid"]) != 0)
+    # total ink mass (inflow included) to the storage's rounding level
+    mg, mo = fg["diag"]["mass"], do["mass"]
+    assert abs(mg[0] / mo[0] - 1) <= 0.1 * TOL16[storage]
+    assert abs(mg[1] / mo[1] - 1) <= 0.01 * TOL16[storage]
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_rest_state_is_exact(storage):
+    """A resting uniform ambient is the zero deviation: stored exactly, it
+    stays exactly at rest."""
+    lbm = _lbm()
+    shape = (40, 16, 16)
+    wl = I.workload("small_print_f64")
+    geom = dict(wl["geom"], nozzle=0, z_mode=0)
+    lat = lbm.Lattice(shape, dict(wl["params"], storage=storage), geom, wl["rheo"], path="plain")
+    lat.set_fields(np.zeros(shape[::-1]), np.ones(shape[::-1]))
+    lat.step(50)
+    fg = lat.fields()
+    lat.close()
+    assert np.all(fg["rho_amb"] == 1.0) and np.all(fg["rho_ink"] == 0.0)
+    for c in ("ux", "uy", "uz"):
+        assert np.all(fg[c] == 0.0)
+
+
+def test_fp16_ragged_lattice_both_paths_agree_with_oracle():
+    """A lattice whose x and y are not multiples of the tile (ragged tiles and
+    periodic wrap in the fused kernel), FP16 storage, 60 steps."""
+    lbm = _lbm()
+    shape = (45, 27, 30)
+    wl = I.print_run(shape, 4.0, 10, 0.01, 0.02, 0.6, "f16dev", head_pos=(12.0, 13.0))
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=3))
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f64"), geom=wl["geom"], rheo=wl["rheo"])
+    ref.set_fields(rY, rB)
+    ref.step(60)
+    fo = ref.fields()
+    for path in ("plain", "fused"):
+        lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path=path)
+        lat.set_fields(rY, rB)
+        lat.step(60)
+        fg = lat.fields()
+        lat.close()
+        e = field_errors(fg, fo, HYDRO)
+        assert max(e.values()) <= TOL16["f16dev"], (path, e)
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden file not generated")
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+def test_print_128x64x64_10k_steps(storage):
+    """The 128x64x64 print run over 10,000 steps against the stored oracle
+    result (sampled every 4th site): the per-field error after a long run,
+    reported, with a bar that catches a broken storage mode."""
+    lbm = _lbm()
+    g = np.load(GOLDEN)
+    wl = I.workload("print_128x64x64")
+    shape = wl["shape"]
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=0))
+    lat = lbm.Lattice(shape, dict(wl["params"], storage=storage), wl["geom"], wl["rheo"], path="fused")
+    lat.set_fields(rY, rB)
+    lat.step(int(g["steps"]))
+    fg = lat.fields()
+    lat.close()
+    sub = int(g["sub"])
+    uscale = max(float(g["speed_max"]), 1e-2)
+    errs = {}
+    for k in ("rho_ink", "rho_amb", "ux", "uy", "uz"):
+        a = np.asarray(fg[k], dtype=np.float64)[::sub, ::sub, ::sub]
+        scale = uscale if k.startswith("u") else float(g["scale_" + k])
+        errs[k] = float(np.abs(a - g[k]).max() / scale)
+    print("10k-step errors", storage, {k: "%.2e" % v for k, v in errs.items()})
+    bar = {"f32": 1e-3, "f16dev": 5e-2, "bf16dev": 3e-1}[storage]
+    assert max(errs.values()) <= bar, errs
