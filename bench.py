@@ -268,6 +268,12 @@ def run_ours(args):
     e2e, unstable = None, 0
     if not args.no_e2e:
         e2e, unstable = run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws)
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        lat.close()
+        lat = None
+        torch.cuda.empty_cache()
+        sweep = run_sweep(args, local)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O
@@ -276,7 +282,8 @@ def run_ours(args):
         cpu = {"value": mlups, "unit": "MLUPS", "cores": O.threads_used(), "kind": "oracle",
                "sample": "%s full lattice (%d sites), %d steps after 1 untimed, %.1f s" % (args.workload, n, cs, dt)}
 
-    lat.close()
+    if lat is not None:
+        lat.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -287,10 +294,79 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (populations %.2f GB)" % (BYTES_PER_SITE[storage] * nsites / 1e9),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "unstable": unstable}
+                "clocks": clk.summary(), "unstable": unstable, "sweep": sweep}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def sweep_workloads(n=64, seed=2024):
+    """The batched parameter sweep: n print runs from 96^3 to 256x96x96, nozzle
+    radius 4-12, power-law n in [0.3, 1.0], extrusion 0.01-0.05, head speed
+    0-0.02 l.u./step, drawn from the seed (FP32)."""
+    import numpy as np
+    from paper_2102_02655_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.choice([96, 128, 160, 192, 224, 256]))
+        shape = (nx, 96, 96)
+        out.append(I.print_run(shape, float(rng.uniform(4.0, 12.0)), 20, float(rng.uniform(0.0, 0.02)),
+                               float(rng.uniform(0.01, 0.05)), float(rng.uniform(0.3, 1.0)), "f32",
+                               head_pos=(nx / 4.0, 48.0)))
+    return out
+
+
+def run_sweep(args, device):
+    """Batched sweep vs the plain one-lattice-at-a-time form on the same
+    lattices: whole-sweep MLUPS and simulations per hour at 10k steps each."""
+    import torch
+    from paper_2102_02655_gb300 import inputs as I, lbm
+    wls = sweep_workloads(args.sweep_n)
+    lats = []
+    for k, wl in enumerate(wls):
+        lat = lbm.Lattice(wl["shape"], wl["params"], wl["geom"], wl["rheo"], path="fused", device=device)
+        rY, rB = I.nozzle_fill(wl["shape"], wl["geom"])
+        lat.set_fields(rY, I.perturbed_ambient(wl["shape"], rB, seed=k))
+        lats.append(lat)
+    sites = sum(w["shape"][0] * w["shape"][1] * w["shape"][2] for w in wls)
+    K = args.sweep_steps
+    torch.cuda.synchronize()
+    # plain form: one lattice after another, each K steps on its own stream
+    for lat in lats:
+        lat.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in lats:
+        lat.step(K)
+        lat.stream.synchronize()
+    t_plain = time.perf_counter() - t0
+    # batched form: autotuned plan, K steps as replayed graphs
+    batch = lbm.Batch(lats)
+    tune = batch.autotune(trial_steps=4)
+    batch.step(K)  # warm-up (graph capture)
+    batch.sync()
+    t0 = time.perf_counter()
+    batch.step(K)
+    batch.sync()
+    t_batch = time.perf_counter() - t0
+    info = batch.info()
+    bad = sum(lat.diag()["unstable"] for lat in lats)
+    batch.close()
+    for lat in lats:
+        lat.close()
+    steps_per_sim = 10000
+    return {"lattices": len(wls), "sites": sites, "steps_timed": K,
+            "plain_mlups": sites * K / t_plain / 1e6, "batched_mlups": sites * K / t_batch / 1e6,
+            "speedup": t_plain / t_batch,
+            "plain_sims_per_hour": len(wls) * 3600.0 / (t_plain / K * steps_per_sim),
+            "batched_sims_per_hour": len(wls) * 3600.0 / (t_batch / K * steps_per_sim),
+            "sims_per_hour_note": "10k-step simulations; plain = one after another, batched = all together",
+            "autotune": {"variant": tune["variant"], "zchunk": tune["zchunk"],
+                         "ms_per_step": tune["ms_per_step"], "candidates": len(tune["tried"])},
+            "graph_steps": info["steps_per_graph"], "work_items": info["n_items"], "grid": info["grid"],
+            "unstable": bad,
+            "what": "64 print runs 96^3..256x96x96 (seeded parameters), wall time of K steps, host-synchronised"}
 
 
 def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
@@ -327,6 +403,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched parameter sweep")
+    ap.add_argument("--sweep-n", type=int, default=64)
+    ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--storage", choices=["f64", "f32", "f16dev", "bf16dev"], default=None,
                     help="population storage (default: the workload's, FP32)")
     ap.add_argument("--workload", default=WORKLOAD,

@@ -247,6 +247,73 @@ lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry* g, const 
 
 typedef struct lbm_handle lbm_handle;
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent lattices (a parameter sweep of print runs,
+ * Sec. III) advanced together on one device. Each lattice keeps its own
+ * handle, state and parameters; per time step (Eq. 1) one persistent launch
+ * covers the bulk of every lattice and one launch per phase covers every
+ * nozzle box, and G steps at a time run as one replayed CUDA graph. Every
+ * lattice computes exactly what lbm_step computes on it alone, whatever the
+ * plan (tile height, z-planes per column).
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Group n lattices (host array of handles, not copied beyond this call;
+ * the handles stay owned by the caller and must outlive the batch). Every
+ * lattice must be configured (geometry and rheology set), take the fused path
+ * (D3Q19, substrate below, open top, 38 N < 2^31), and share the device, the
+ * storage and the density-ratio class (ratio one or not) with the others;
+ * nx <= 65535, ny <= 32767. Returns LBM_EINVAL / LBM_ESTATE otherwise (message
+ * from lbm_batch_last_error(NULL)), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out);
+
+/* Advance every lattice of the batch by nsteps steps (asynchronous on the
+ * batch's own stream, ordered after work already enqueued on each lattice's
+ * stream and before work enqueued there later). The fields of the last step
+ * are kept for lbm_fields on each handle. */
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+
+/* Wait for the batch's stream. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+
+/* Set the plan: variant 0 (32 x 8 tile columns) or 1 (32 x 16, FP32 and
+ * 16-bit storage only) and, per lattice (host array of n ints), the z-planes
+ * each column of the bulk kernel marches. Waits for the batch's stream. */
+lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk);
+
+/* Autotuner: times trial_steps real steps of the batch (after one untimed
+ * graph capture) for each candidate plan (variant x z-planes per column in
+ * 8 .. 128 up to the tallest lattice) and keeps the fastest. The trial steps
+ * advance the lattices (every candidate computes the same result). */
+#define LBM_TUNE_MAX 32
+typedef struct {
+    int variant, zchunk;      /* chosen plan */
+    double ms_per_step;       /* its time per batch step */
+    int n_tried;              /* candidates timed */
+    int tried_variant[LBM_TUNE_MAX], tried_zchunk[LBM_TUNE_MAX];
+    double tried_ms[LBM_TUNE_MAX];
+} lbm_batch_tuning;
+lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* out);
+
+typedef struct {
+    int n_lattices, variant, tile_h, n_items, grid, steps_per_graph;
+    long long steps, launches;  /* batch steps taken, kernels launched by them */
+} lbm_batch_plan_info;
+lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_plan_info* out);
+
+/* Release the batch (not its lattices). NULL is accepted. */
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Message of the last failing call on b (NULL: of the last lbm_batch_create). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Host-only helper (no device work): the work list of the persistent bulk
+ * kernel for n lattices of sizes dims[3l..3l+2] = (nx, ny, nz), tile height
+ * tile_h and z-planes per column zchunk[l]. Writes up to cap items of four
+ * ints (lattice, x0 | y0 << 16, za, zb) to items (may be NULL) and returns
+ * the item count, or -1 for invalid arguments. */
+long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 #include <new>
 #include <thread>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.h"
@@ -237,9 +238,10 @@ Region grow(const Region& r, int k, int nx, int ny, int nz) {
     return o;
 }
 
-// box around the nozzle wall at steps n-1 and n, with kBoxMargin sites of margin
+// box around the nozzle wall at steps n0 and n0 + 1 (the step that n0 + 1
+// completes), with kBoxMargin sites of margin
 template <typename real>
-Region nozzle_box(const lbm_handle* h, const StepArgs<real>& p) {
+Region nozzle_box(const lbm_handle* h, const StepArgs<real>& p, long long n0) {
     const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
     if (!p.nozzle) return Region{0, 0, 0, 0, 0, 0};
     const long long ro = q20(h->geom.r_inner + h->geom.wall_thickness);
@@ -247,7 +249,7 @@ Region nozzle_box(const lbm_handle* h, const StepArgs<real>& p) {
     const lbm_geometry& g = h->geom;
     const long long hx0 = q20(g.head_pos[0]), hy0 = q20(g.head_pos[1]);
     const long long vx = q20(g.head_vel[0]), vy = q20(g.head_vel[1]);
-    const long long n1 = h->step + 1, n0 = h->step;
+    const long long n1 = n0 + 1;
     const long long ax[2] = {hx0 + vx * n0, hx0 + vx * n1}, ay[2] = {hy0 + vy * n0, hy0 + vy * n1};
     const long long xlo = floor_div(std::min(ax[0], ax[1]) - ro, fx) - kBoxMargin;
     const long long xhi = floor_div(std::max(ax[0], ax[1]) + ro, fx) + 1 + kBoxMargin;
@@ -326,7 +328,7 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
         int launched = 0;
         lbm_status st = LBM_OK;
         if (std::is_same<VS, D3Q19>::value && is_fused(h)) {
-            const Region box = nozzle_box(h, p);
+            const Region box = nozzle_box(h, p, h->step);
             p.box = box;
             const long long box_sites = (long long)box.wx * box.wy * (box.z1 - box.z0);
             if (box.wx > 0) {
@@ -851,3 +853,499 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry
     return cfg->storage == LBM_F64 ? noalloc_step<D2Q9, double>(&tmp, step, f_in, f_out, fields, diag, scratch, stream)
                                    : noalloc_step<D2Q9, float>(&tmp, step, f_in, f_out, fields, diag, scratch, stream);
 }
+
+// ---------------------------------------------------------------------------
+// Batches: many lattices advanced together. Per step, one persistent launch
+// covers the bulk of every lattice (a work list of tile columns), and one
+// launch per phase covers the nozzle boxes of every lattice; G steps are
+// captured once in a CUDA graph and replayed, each replay reading the step
+// arguments of its G steps from a device table the host refreshes.
+// ---------------------------------------------------------------------------
+
+struct lbm_batch {
+    std::vector<lbm_handle*> lat;
+    int device = 0, storage = LBM_F32, unit = 1;
+    cudaStream_t stream = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+    std::vector<cudaEvent_t> hev;  // one per lattice: its stream's work before the batch's
+    // plan: fused-kernel variant, z-planes per column for each lattice
+    int variant = 0;
+    std::vector<int> zchunk;
+    int4* d_items = nullptr;
+    size_t items_cap = 0;
+    int* d_queue = nullptr;  // one work-queue counter per captured step
+    int n_items = 0, grid = 0;
+    unsigned box_gx = 0, box_gy = 0;
+    // step tables: [G][L] StepArgs, then [G][L] BoxArgs
+    int G = 16;
+    size_t args_bytes = 0, box_bytes = 0;
+    void* d_tab = nullptr;
+    void* h_tab[2] = {nullptr, nullptr};
+    cudaEvent_t h_ev[2] = {nullptr, nullptr};
+    int hbuf = 0;
+    // captured graphs: [0] for G steps, [1] for the last remainder size
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int exec_g[2] = {0, 0};
+    bool exec_valid = false;
+    long long launches = 0, steps = 0;
+    bool dead = false;
+    char err[256] = "";
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status st, const char* fmt, ...) {
+    char* dst = b ? b->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lbm_status bcuda(lbm_batch* b, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LBM_OK;
+    b->dead = true;
+    return bfail(b, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Work list of the persistent bulk kernel: for each lattice, its tile columns
+// (32 x tile_h sites) of each z-chunk, lattice-major then chunk, row, column,
+// so that the CTAs running at one time work on neighbouring columns of one
+// lattice (their halo re-reads then hit L2). Returns the item count; writes
+// at most cap items.
+long long plan_items(const int* dims, int n, int tile_h, const int* zchunk, int* out, long long cap) {
+    long long k = 0;
+    for (int l = 0; l < n; ++l) {
+        const int nx = dims[3 * l], ny = dims[3 * l + 1], nz = dims[3 * l + 2];
+        const int zc = std::max(1, zchunk[l]);
+        for (int za = 0; za < nz; za += zc)
+            for (int y0 = 0; y0 < ny; y0 += tile_h)
+                for (int x0 = 0; x0 < nx; x0 += 32) {
+                    if (k < cap && out) {
+                        out[4 * k] = l;
+                        out[4 * k + 1] = x0 | (y0 << 16);
+                        out[4 * k + 2] = za;
+                        out[4 * k + 3] = std::min(nz, za + zc);
+                    }
+                    ++k;
+                }
+    }
+    return k;
+}
+
+template <typename real, typename S>
+lbm_status batch_plan(lbm_batch* b, int variant, const std::vector<int>& zc) {
+    const int L = (int)b->lat.size();
+    const bool fp64 = sizeof(real) == 8;
+    const int th = fused_tile_height(variant, fp64);
+    std::vector<int> dims(3 * L);
+    for (int l = 0; l < L; ++l) {
+        dims[3 * l] = b->lat[l]->cfg.nx;
+        dims[3 * l + 1] = b->lat[l]->cfg.ny;
+        dims[3 * l + 2] = b->lat[l]->cfg.nz;
+    }
+    const long long n = plan_items(dims.data(), L, th, zc.data(), nullptr, 0);
+    if (n > 0x7fffffffLL) return bfail(b, LBM_EINVAL, "lbm_batch: work list too long");
+    std::vector<int> items(4 * n);
+    plan_items(dims.data(), L, th, zc.data(), items.data(), n);
+    cudaError_t e = cudaSuccess;
+    if ((size_t)n > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        e = cudaMalloc(&b->d_items, (size_t)n * sizeof(int4));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->items_cap = 0;
+            return bfail(b, LBM_ENOMEM, "lbm_batch: work list allocation failed");
+        }
+        b->items_cap = (size_t)n;
+    }
+    e = cudaMemcpyAsync(b->d_items, items.data(), (size_t)n * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch: work list upload");
+    int occ = 0, sms = 0;
+    launch_fused_batch<real, S>(nullptr, nullptr, 0, nullptr, 0, b->unit, variant, b->stream, &occ);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaDeviceGetAttribute");
+    b->n_items = (int)n;
+    b->grid = (int)std::max(1LL, std::min<long long>(n, (long long)std::max(1, occ) * sms));
+    b->variant = variant;
+    b->zchunk = zc;
+    b->exec_valid = false;
+    return LBM_OK;
+}
+
+// grid of the batched box kernels: the largest grown box (columns, planes)
+// with two sites of slack per side, so that the box can move for a while
+// before the captured graph needs a larger grid
+void box_grid(const Region& R2, const Region& R1g, unsigned* gx, unsigned* gy) {
+    const long long cols = (long long)(R2.wx + 4) * (R2.wy + 4);
+    *gx = std::max(*gx, (unsigned)((cols + 255) / 256));
+    *gy = std::max(*gy, (unsigned)std::max(R2.z1 - R2.z0, R1g.z1 - R1g.z0));
+}
+
+template <typename real, typename S>
+lbm_status batch_capture(lbm_batch* b, int slot, int g) {
+    if (b->exec[slot]) {
+        cudaGraphExecDestroy(b->exec[slot]);
+        b->exec[slot] = nullptr;
+    }
+    const int L = (int)b->lat.size();
+    const StepArgs<real>* args = (const StepArgs<real>*)b->d_tab;
+    const BoxArgs<real>* box = (const BoxArgs<real>*)((const char*)b->d_tab + (size_t)b->G * L * sizeof(StepArgs<real>));
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch: begin capture");
+    for (int k = 0; k < g && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+        if (e != cudaSuccess) break;
+        launch_plain_batch<D3Q19, real, S>(box + (size_t)k * L, L, b->box_gx, b->box_gy, b->unit, b->side);
+        e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) break;
+        launch_fused_batch<real, S>(args + (size_t)k * L, b->d_items, b->n_items, b->d_queue + k, b->grid, b->unit,
+                                    b->variant, b->stream, nullptr);
+        e = cudaEventRecord(b->join, b->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch: graph capture");
+    b->exec_g[slot] = g;
+    return LBM_OK;
+}
+
+template <typename real, typename S>
+lbm_status batch_steps(lbm_batch* b, int nsteps) {
+    const int L = (int)b->lat.size();
+    cudaError_t e = cudaSuccess;
+    // the batch's work follows whatever was enqueued on each lattice's stream
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+        e = cudaEventRecord(b->hev[l], b->lat[l]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->hev[l], 0);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step: order after the lattices' streams");
+    int remaining = nsteps;
+    while (remaining > 0) {
+        const int g = std::min(b->G, remaining);
+        const bool last = remaining == g;
+        const int buf = b->hbuf;
+        e = cudaEventSynchronize(b->h_ev[buf]);  // the previous upload from this host buffer is done
+        if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step: host table");
+        StepArgs<real>* ha = (StepArgs<real>*)b->h_tab[buf];
+        BoxArgs<real>* hb = (BoxArgs<real>*)((char*)b->h_tab[buf] + (size_t)b->G * L * sizeof(StepArgs<real>));
+        unsigned gx = b->box_gx, gy = b->box_gy;
+        for (int k = 0; k < g; ++k) {
+            for (int l = 0; l < L; ++l) {
+                lbm_handle* h = b->lat[l];
+                StepArgs<real>& p = ha[(size_t)k * L + l];
+                memset(&p, 0, sizeof(p));
+                fill_model(h, p);
+                fill_geometry(h, p, h->step + 1 + k);
+                fill_buffers(h, p, h->cur ^ (k & 1));
+                p.write_fields = (last && k == g - 1) ? 1 : 0;
+                const Region box = nozzle_box(h, p, h->step + k);
+                p.box = box;
+                BoxArgs<real>& q = hb[(size_t)k * L + l];
+                memset(&q, 0, sizeof(q));
+                q.p = p;
+                q.R = box;
+                if (box.wx > 0) {
+                    const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
+                    q.R1 = grow(box, 1, nx, ny, nz);
+                    q.R2 = grow(box, 2, nx, ny, nz);
+                    q.R1g = q.R1;
+                    if (q.R1g.z0 <= 0) q.R1g.z0 = -1;
+                    if (q.R1g.z1 >= nz) q.R1g.z1 = nz + 1;
+                    box_grid(q.R2, q.R1g, &gx, &gy);
+                }
+            }
+        }
+        if (gx > b->box_gx || gy > b->box_gy) {
+            // a box outgrew the captured grid: widen it (with slack) and recapture
+            b->box_gx = gx + gx / 4 + 1;
+            b->box_gy = gy;
+            b->exec_valid = false;
+        }
+        e = cudaMemcpyAsync(b->d_tab, b->h_tab[buf], b->args_bytes + b->box_bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->h_ev[buf], b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step: table upload");
+        b->hbuf ^= 1;
+        if (last) {
+            for (int l = 0; l < L && e == cudaSuccess; ++l)
+                e = cudaMemsetAsync(b->lat[l]->acc + kAccMass, 0, 5 * sizeof(double), b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
+        }
+        if (!b->exec_valid) b->exec_g[0] = b->exec_g[1] = 0;
+        b->exec_valid = true;
+        const int slot = g == b->G ? 0 : 1;
+        if (b->exec_g[slot] != g) {
+            lbm_status st = batch_capture<real, S>(b, slot, g);
+            if (st != LBM_OK) return st;
+        }
+        e = cudaGraphLaunch(b->exec[slot], b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "cudaGraphLaunch");
+        for (int l = 0; l < L; ++l) {
+            lbm_handle* h = b->lat[l];
+            h->step += g;
+            h->cur ^= (g & 1);
+        }
+        b->launches += 5LL * g;
+        b->steps += g;
+        remaining -= g;
+    }
+    // later work on each lattice's stream (lbm_fields, lbm_step) follows the batch
+    e = cudaEventRecord(b->done, b->stream);
+    for (int l = 0; l < L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lat[l]->stream, b->done, 0);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step: order before the lattices' streams");
+    return LBM_OK;
+}
+
+template <typename real, typename S>
+lbm_status batch_alloc_tables(lbm_batch* b) {
+    const int L = (int)b->lat.size();
+    b->args_bytes = (size_t)b->G * L * sizeof(StepArgs<real>);
+    b->box_bytes = (size_t)b->G * L * sizeof(BoxArgs<real>);
+    const size_t bytes = b->args_bytes + b->box_bytes;
+    cudaError_t e = cudaMalloc(&b->d_tab, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, (size_t)b->G * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tab[0], bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tab[1], bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LBM_ENOMEM, "lbm_batch_create: step tables (%.1f MB)", 3.0 * bytes / 1e6);
+    }
+    return LBM_OK;
+}
+
+// dispatch on the batch's storage (all lattices share it)
+template <template <typename, typename> class F, typename... A>
+lbm_status batch_dispatch(lbm_batch* b, A... a) {
+    switch (b->storage) {
+    case LBM_F64: return F<double, double>::run(b, a...);
+    case LBM_F16DEV: return F<float, __half>::run(b, a...);
+    case LBM_BF16DEV: return F<float, __nv_bfloat16>::run(b, a...);
+    default: return F<float, float>::run(b, a...);
+    }
+}
+template <typename real, typename S>
+struct RunSteps {
+    static lbm_status run(lbm_batch* b, int n) { return batch_steps<real, S>(b, n); }
+};
+template <typename real, typename S>
+struct RunPlan {
+    static lbm_status run(lbm_batch* b, int variant, const std::vector<int>* zc) { return batch_plan<real, S>(b, variant, *zc); }
+};
+template <typename real, typename S>
+struct RunAlloc {
+    static lbm_status run(lbm_batch* b) { return batch_alloc_tables<real, S>(b); }
+};
+
+lbm_status batch_usable(lbm_batch* b) {
+    if (!b) return LBM_EINVAL;
+    if (b->dead) return bfail(b, LBM_ECUDA, "batch unusable after an earlier CUDA error");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaSetDevice");
+    for (lbm_handle* h : b->lat)
+        if (h->dead) return bfail(b, LBM_ECUDA, "a lattice of the batch is unusable after a CUDA error");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap) {
+    if (!dims || !zchunk || n < 0 || tile_h < 1) return -1;
+    for (int l = 0; l < n; ++l)
+        if (dims[3 * l] < 1 || dims[3 * l + 1] < 1 || dims[3 * l + 2] < 1 || dims[3 * l] > 65535 ||
+            dims[3 * l + 1] > 32767)
+            return -1;
+    return plan_items(dims, n, tile_h, zchunk, items, items ? cap : 0);
+}
+
+lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: out is NULL");
+    *out = nullptr;
+    if (!lattices || n < 1) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: need at least one lattice");
+    int unit0 = -1;
+    for (int l = 0; l < n; ++l) {
+        lbm_handle* h = lattices[l];
+        if (!h) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d is NULL", l);
+        if (h->dead) return bfail(nullptr, LBM_ECUDA, "lbm_batch_create: lattice %d is unusable", l);
+        if (!h->have_geom || !h->have_rheo)
+            return bfail(nullptr, LBM_ESTATE, "lbm_batch_create: lattice %d has no geometry or rheology", l);
+        if (!is_fused(h))
+            return bfail(nullptr, LBM_EINVAL,
+                         "lbm_batch_create: lattice %d is not a fused-path lattice (D3Q19, substrate + open top)", l);
+        if (h->cfg.nx > 65535 || h->cfg.ny > 32767)
+            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d too wide for the work list", l);
+        if (h->cfg.device != lattices[0]->cfg.device || h->cfg.storage != lattices[0]->cfg.storage)
+            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattices must share device and storage");
+        for (int m = 0; m < l; ++m)
+            if (lattices[m] == h) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d given twice", l);
+        StepArgs<double> p;
+        memset(&p, 0, sizeof(p));
+        fill_model(h, p);
+        if (unit0 < 0) unit0 = p.unit;
+        if (p.unit != unit0)
+            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattices must all have density ratio one or none");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: host allocation failed");
+    b->lat.assign(lattices, lattices + n);
+    b->device = lattices[0]->cfg.device;
+    b->storage = lattices[0]->cfg.storage;
+    b->unit = unit0;
+    b->hev.assign(n, nullptr);
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&b->fork, &b->join, &b->done, &b->h_ev[0], &b->h_ev[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+    for (int l = 0; l < n && e == cudaSuccess; ++l) e = cudaEventCreateWithFlags(&b->hev[l], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        bfail(nullptr, LBM_ECUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
+        lbm_batch_destroy(b);
+        return LBM_ECUDA;
+    }
+    lbm_status st = batch_dispatch<RunAlloc>(b);
+    if (st == LBM_OK) {
+        // default plan: the single-lattice heuristic's z-chunk for each lattice
+        std::vector<int> zc(n);
+        for (int l = 0; l < n; ++l) zc[l] = lattices[l]->zchunk;
+        st = batch_dispatch<RunPlan>(b, 0, &zc);
+    }
+    if (st != LBM_OK) {
+        snprintf(g_create_error, sizeof(g_create_error), "%s", b->err);
+        lbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
+    lbm_status st = batch_usable(b);
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    return batch_dispatch<RunSteps>(b, nsteps);
+}
+
+lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk) {
+    lbm_status st = batch_usable(b);
+    if (st != LBM_OK) return st;
+    if (variant < 0 || variant > 1) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: variant must be 0 or 1");
+    if (!zchunk) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: zchunk is NULL");
+    std::vector<int> zc(zchunk, zchunk + b->lat.size());
+    for (int v : zc)
+        if (v < 1) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: z-chunks must be >= 1");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_set_plan: sync");
+    return batch_dispatch<RunPlan>(b, variant, &zc);
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* out) {
+    lbm_status st = batch_usable(b);
+    if (st != LBM_OK) return st;
+    if (trial_steps < 1) return bfail(b, LBM_EINVAL, "lbm_batch_autotune: trial_steps < 1");
+    const int L = (int)b->lat.size();
+    int max_nz = 1;
+    for (lbm_handle* h : b->lat) max_nz = std::max(max_nz, h->cfg.nz);
+    const int chunks[] = {8, 12, 16, 24, 32, 48, 64, 96, 128};
+    const int nvar = b->storage == LBM_F64 ? 1 : 2;
+    lbm_batch_tuning res;
+    memset(&res, 0, sizeof(res));
+    res.ms_per_step = 1e30;
+    for (int v = 0; v < nvar; ++v) {
+        for (int c : chunks) {
+            if (c > max_nz && c != chunks[0]) continue;
+            std::vector<int> zc(L, c);
+            cudaError_t e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: sync");
+            if ((st = batch_dispatch<RunPlan>(b, v, &zc)) != LBM_OK) return st;
+            // the first call captures the graph; the second is timed
+            const int g = std::min(b->G, trial_steps);
+            if ((st = lbm_batch_step(b, g)) != LBM_OK) return st;
+            e = cudaEventRecord(b->t0, b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "cudaEventRecord");
+            if ((st = lbm_batch_step(b, trial_steps)) != LBM_OK) return st;
+            e = cudaEventRecord(b->t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->t0, b->t1);
+            if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: timing");
+            const double per = ms / trial_steps;
+            if (res.n_tried < LBM_TUNE_MAX) {
+                res.tried_variant[res.n_tried] = v;
+                res.tried_zchunk[res.n_tried] = c;
+                res.tried_ms[res.n_tried] = per;
+            }
+            res.n_tried += 1;
+            if (per < res.ms_per_step) {
+                res.ms_per_step = per;
+                res.variant = v;
+                res.zchunk = c;
+            }
+        }
+    }
+    std::vector<int> zc(L, res.zchunk);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: sync");
+    if ((st = batch_dispatch<RunPlan>(b, res.variant, &zc)) != LBM_OK) return st;
+    if (out) *out = res;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_plan_info* out) {
+    if (!b || !out) return LBM_EINVAL;
+    out->n_lattices = (int)b->lat.size();
+    out->variant = b->variant;
+    out->tile_h = fused_tile_height(b->variant, b->storage == LBM_F64);
+    out->n_items = b->n_items;
+    out->grid = b->grid;
+    out->steps_per_graph = b->G;
+    out->steps = b->steps;
+    out->launches = b->launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    lbm_status st = batch_usable(b);
+    if (st != LBM_OK) return st;
+    return bcuda(b, cudaStreamSynchronize(b->stream), "lbm_batch_sync");
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->side) cudaStreamSynchronize(b->side);
+    for (cudaGraphExec_t x : b->exec)
+        if (x) cudaGraphExecDestroy(x);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_tab) cudaFree(b->d_tab);
+    if (b->d_queue) cudaFree(b->d_queue);
+    for (int k = 0; k < 2; ++k) {
+        if (b->h_tab[k]) cudaFreeHost(b->h_tab[k]);
+        if (b->h_ev[k]) cudaEventDestroy(b->h_ev[k]);
+    }
+    for (cudaEvent_t ev : {b->fork, b->join, b->done, b->t0, b->t1})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : b->hev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_create_error; }
+
+}  // extern "C"

@@ -116,9 +116,10 @@ struct Region {
     int x0, wx, y0, wy, z0, z1;
 };
 
-// Everything a kernel needs for one step. Passed by value.
+// Everything a kernel needs for one step. Passed by value (or, for batches of
+// lattices, read from a device table; 16-byte aligned for vector copies).
 template <typename real>
-struct StepArgs {
+struct __align__(16) StepArgs {
     int nx, ny, nz;
     long long N;       // sites
     long long plane;   // nx * ny

@@ -210,12 +210,15 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 
 // The own sites' pulled populations wait in shared memory for their
 // collision (one plane later); each thread reads back only its own column.
-template <typename real, typename S, bool kUnit, int TY_, int MINB>
-__global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+// One tile column (x0, y0) of planes [za, zb) of one lattice; shared memory
+// as laid out by fused_smem. Used by the single-lattice kernel (one column
+// per CTA) and by the persistent batched kernel (a list of columns per CTA).
+template <typename real, typename S, bool kUnit, int TY_>
+__device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
+                                             int zb) {
     using T = Tile<TY_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
-    extern __shared__ __align__(16) unsigned char smraw[];
     real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][38][NT]
     Colour<real, kUnit, HS> C{pops + 2 * 38 * NT};  // [4 slots][NV][HS]
     // substrate prologue scratch [2][SS]: population buffer 1, first written
@@ -223,9 +226,6 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
     real* sub = pops + 38 * NT;
     (void)TX;
 
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int za = blockIdx.z * zchunk;
-    const int zb = min(p.nz, za + zchunk);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x = x0 + tx, y = y0 + ty;
     const bool in_xy = x < p.nx && y < p.ny;
@@ -406,6 +406,47 @@ constexpr size_t fused_smem() {
 }
 
 template <typename real, typename S, bool kUnit, int TY_, int MINB>
+__global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int za = blockIdx.z * zchunk;
+    fused_column<real, S, kUnit, TY_>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
+                                      min(p.nz, za + zchunk));
+}
+
+// Persistent form over many lattices: the CTAs take columns of the work list
+// (lattice, x0 | y0 << 16, za, zb) in order from a queue (an atomic counter,
+// zero at launch), so CTAs that become resident late, behind other kernels,
+// simply take fewer columns. Each lattice's step arguments are copied to
+// shared memory when a CTA's column changes lattice.
+template <typename real, typename S, bool kUnit, int TY_, int MINB>
+__global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
+    k_fused_batch(const StepArgs<real>* __restrict__ args, const int4* __restrict__ items, int n_items,
+                  int* __restrict__ queue) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(16) StepArgs<real> sp;
+    __shared__ int next;
+    constexpr int NT = Tile<TY_>::NT;
+    const int tid = threadIdx.y * Tile<TY_>::TX + threadIdx.x;
+    int last = -1;
+    for (;;) {
+        __syncthreads();  // the previous column's shared state and `next` are free
+        if (tid == 0) next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int w = next;
+        if (w >= n_items) break;
+        const int4 it = items[w];
+        if (it.x != last) {
+            const int4* src = reinterpret_cast<const int4*>(args + it.x);
+            int4* dst = reinterpret_cast<int4*>(&sp);
+            for (int k = tid; k < (int)(sizeof(StepArgs<real>) / 16); k += NT) dst[k] = src[k];
+            last = it.x;
+            __syncthreads();
+        }
+        fused_column<real, S, kUnit, TY_>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
+    }
+}
+
+template <typename real, typename S, bool kUnit, int TY_, int MINB>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     using T = Tile<TY_>;
     constexpr size_t smem = fused_smem<real, kUnit, TY_>();
@@ -422,6 +463,37 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
     k_fused<real, S, kUnit, TY_, MINB><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
+}
+
+template <typename real, typename S, bool kUnit, int TY_, int MINB>
+int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
+                     cudaStream_t st, int* occupancy) {
+    constexpr size_t smem = fused_smem<real, kUnit, TY_>();
+    static unsigned configured = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 32 && !(configured & (1u << dev))) {
+        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured |= 1u << dev;
+    }
+    if (occupancy) {
+        *occupancy = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_fused_batch<real, S, kUnit, TY_, MINB>,
+                                                      Tile<TY_>::NT, smem);
+        return 0;
+    }
+    if (n_items <= 0) return 0;
+    k_fused_batch<real, S, kUnit, TY_, MINB><<<grid, dim3(Tile<TY_>::TX, TY_), smem, st>>>(args, items, n_items,
+                                                                                       queue);
+    return 1;
+}
+
+template <typename real, typename S, int TY_, int MINB>
+int batch_variant(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
+                  cudaStream_t st, int* occupancy) {
+    return unit ? launch_batch_one<real, S, true, TY_, MINB>(args, items, n_items, queue, grid, st, occupancy)
+                : launch_batch_one<real, S, false, TY_, MINB>(args, items, n_items, queue, grid, st, occupancy);
 }
 
 template <typename real, typename S, int TY_, int MINB>
@@ -444,6 +516,29 @@ int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int varia
         return launch_variant<real, S, 8, 2>(p, zchunk, st);
     }
 }
+
+int fused_tile_height(int variant, bool fp64) { return (!fp64 && variant == 1) ? 16 : 8; }
+
+template <typename real, typename S>
+int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
+                       int variant, cudaStream_t st, int* occupancy) {
+    if constexpr (sizeof(real) == 8) {
+        (void)variant;
+        return batch_variant<real, S, 8, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
+    } else {
+        if (variant == 1) return batch_variant<real, S, 16, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
+        return batch_variant<real, S, 8, 2>(args, items, n_items, queue, grid, unit, st, occupancy);
+    }
+}
+
+template int launch_fused_batch<float, float>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+                                              cudaStream_t, int*);
+template int launch_fused_batch<double, double>(const StepArgs<double>*, const int4*, int, int*, int, int, int,
+                                              cudaStream_t, int*);
+template int launch_fused_batch<float, __half>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+                                              cudaStream_t, int*);
+template int launch_fused_batch<float, __nv_bfloat16>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+                                              cudaStream_t, int*);
 
 template int launch_fused<float, float>(const StepArgs<float>&, int, cudaStream_t, int);
 template int launch_fused<double, double>(const StepArgs<double>&, int, cudaStream_t, int);

@@ -23,6 +23,30 @@ int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, con
 template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant);
 
+// Persistent fused bulk step over many lattices in one launch: grid CTAs take
+// the work list items (lattice index, x0 | y0 << 16, za, zb: one tile column
+// of planes [za, zb)) in order through the counter *queue (zero at launch),
+// reading each lattice's StepArgs from args (device). All lattices share the
+// kernel configuration (unit flag, variant). With occupancy != NULL nothing
+// is launched and the resident CTAs per SM of that configuration are
+// returned there.
+template <typename real, typename S>
+int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
+                       int variant, cudaStream_t st, int* occupancy);
+int fused_tile_height(int variant, bool fp64);
+
+// Batched phase-by-phase step of the nozzle boxes of many lattices: one
+// launch per phase over all lattices (blockIdx.z), each lattice's StepArgs
+// and regions read from the device table t; gx, gy: the largest grid of a
+// lattice's grown box (columns, planes).
+template <typename real>
+struct BoxArgs {
+    StepArgs<real> p;
+    Region R, R1, R2, R1g;
+};
+template <class VS, typename real, typename S>
+int launch_plain_batch(const BoxArgs<real>* t, int n, unsigned gx, unsigned gy, int unit, cudaStream_t st);
+
 // Equilibrium initialisation from fields staged in p.fields (rho_ink, rho_amb,
 // ux, uy, uz planes; u optional) or, when staged == 0, from the print-setup
 // default (ink inside the nozzle above the gap, ambient elsewhere, at rest).

@@ -12,10 +12,11 @@ namespace {
 constexpr int kThreads = 256;
 
 // Launch shape of a region: blockIdx.x covers the region's columns (32-bit),
-// blockIdx.y its planes. Returns false for threads past the last column.
+// blockIdx.y its planes. Returns false for threads past the last column or
+// plane (a batched launch covers the largest region of its lattices).
 __device__ __forceinline__ bool region_site(const Region& r, int nx, int ny, int* x, int* y, int* z) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= r.wx * r.wy) return false;
+    if (t >= r.wx * r.wy || (int)blockIdx.y >= r.z1 - r.z0) return false;
     const int j = t / r.wx;
     const int i = t - j * r.wx;
     *x = wrapn(r.x0 + i, nx);
@@ -56,7 +57,7 @@ inline dim3 region_grid(const Region& r) {
 
 // 1. stream + densities (post-streaming) of every fluid node of step n-1 in R2
 template <class VS, typename real, typename S>
-__global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p, Region R2, Region R) {
+__device__ __forceinline__ void stream_density_body(const StepArgs<real>& p, const Region& R2, const Region& R) {
     const long long comp = p.N + 2 * p.plane;
     double bc0 = 0, bc1 = 0, de0 = 0, de1 = 0;
     int x, y, z;
@@ -93,10 +94,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p
     warp_add(p.acc + kAccDestroyed + 1, de1);
 }
 
+template <class VS, typename real, typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_density(StepArgs<real> p, Region R2, Region R) {
+    stream_density_body<VS, real, S>(p, R2, R);
+}
+
+template <class VS, typename real, typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_stream_density_b(const BoxArgs<real>* __restrict__ t) {
+    const BoxArgs<real>& b = t[blockIdx.z];
+    if (b.R.wx == 0) return;  // no box for this lattice
+    stream_density_body<VS, real, S>(b.p, b.R2, b.R);
+}
+
 // 2. nodes the nozzle uncovered: mean density of the neighbours that are fluid
 //    at both steps (Sec. II B)
 template <class VS, typename real, typename S>
-__global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R1, Region R) {
+__device__ __forceinline__ void created_body(const StepArgs<real>& p, const Region& R1, const Region& R) {
     const long long comp = p.N + 2 * p.plane;
     double c0 = 0, c1 = 0;
     int x, y, z;
@@ -141,6 +154,18 @@ __global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R
     warp_add(p.acc + kAccCreated + 1, c1);
 }
 
+template <class VS, typename real, typename S>
+__global__ void __launch_bounds__(kThreads) k_created(StepArgs<real> p, Region R1, Region R) {
+    created_body<VS, real, S>(p, R1, R);
+}
+
+template <class VS, typename real, typename S>
+__global__ void __launch_bounds__(kThreads) k_created_b(const BoxArgs<real>* __restrict__ t) {
+    const BoxArgs<real>& b = t[blockIdx.z];
+    if (b.R.wx == 0) return;  // no box for this lattice
+    created_body<VS, real, S>(b.p, b.R1, b.R);
+}
+
 // fictitious density of solid node (x, y, z) of step n (Eq. 18): the
 // zeta-scaled, w-weighted mean over its fluid neighbours
 template <class VS, typename real>
@@ -166,7 +191,7 @@ __device__ __forceinline__ void wall_rho(const StepArgs<real>& p, int x, int y, 
 
 // 3. wall densities on solid nodes of R1 and the ghost planes z = -1, z = nz
 template <class VS, typename real>
-__global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g) {
+__device__ __forceinline__ void wall_body(const StepArgs<real>& p, const Region& R1g) {
     const long long comp = p.N + 2 * p.plane;
     int x, y, z;
     if (!region_site(R1g, p.nx, p.ny, &x, &y, &z)) return;
@@ -195,6 +220,18 @@ __global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g)
         p.rho_cur[r] = o0;
         p.rho_cur[comp + r] = o1;
     }
+}
+
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_wall(StepArgs<real> p, Region R1g) {
+    wall_body<VS, real>(p, R1g);
+}
+
+template <class VS, typename real>
+__global__ void __launch_bounds__(kThreads) k_wall_b(const BoxArgs<real>* __restrict__ t) {
+    const BoxArgs<real>& b = t[blockIdx.z];
+    if (b.R.wx == 0) return;  // no box for this lattice
+    wall_body<VS, real>(b.p, b.R1g);
 }
 
 // neighbour accessors over the density array of the step: the ink fraction
@@ -249,7 +286,7 @@ __device__ __forceinline__ void store_fields(const StepArgs<real>& p, long long 
 // 4. collision at every fluid node of step n in R, in place: steps 1 and 2
 //    left the post-streaming (or created) populations in fout
 template <class VS, typename real, bool kUnit, typename S>
-__global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Region R) {
+__device__ __forceinline__ void collide_body(const StepArgs<real>& p, const Region& R) {
     const long long comp = p.N + 2 * p.plane;
     double m0 = 0, m1 = 0, px = 0, py = 0, pz = 0;
     int bad = 0;
@@ -298,6 +335,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Regio
         warp_add(p.acc + kAccMom + 2, pz);
     }
     if (bad) atomicOr(p.flags, 1);
+}
+
+template <class VS, typename real, bool kUnit, typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Region R) {
+    collide_body<VS, real, kUnit, S>(p, R);
+}
+
+template <class VS, typename real, bool kUnit, typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_collide_b(const BoxArgs<real>* __restrict__ t) {
+    const BoxArgs<real>& b = t[blockIdx.z];
+    if (b.R.wx == 0) return;  // no box for this lattice
+    collide_body<VS, real, kUnit, S>(b.p, b.R);
 }
 
 // initial equilibrium state
@@ -403,6 +452,10 @@ int launch_prev_from_f(const StepArgs<real>& p, real* rho_prev, real* u_prev, cu
     return 1;
 }
 
+template int launch_plain_batch<D3Q19, float, float>(const BoxArgs<float>*, int, unsigned, unsigned, int, cudaStream_t);
+template int launch_plain_batch<D3Q19, double, double>(const BoxArgs<double>*, int, unsigned, unsigned, int, cudaStream_t);
+template int launch_plain_batch<D3Q19, float, __half>(const BoxArgs<float>*, int, unsigned, unsigned, int, cudaStream_t);
+template int launch_plain_batch<D3Q19, float, __nv_bfloat16>(const BoxArgs<float>*, int, unsigned, unsigned, int, cudaStream_t);
 template int launch_prev_from_f<D3Q19, float>(const StepArgs<float>&, float*, float*, cudaStream_t);
 template int launch_prev_from_f<D3Q19, double>(const StepArgs<double>&, double*, double*, cudaStream_t);
 template int launch_prev_from_f<D2Q9, float>(const StepArgs<float>&, float*, float*, cudaStream_t);
@@ -421,6 +474,18 @@ int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, con
     k_wall<VS, real><<<region_grid(R1g), kThreads, 0, st>>>(p, R1g);
     if (p.unit) k_collide<VS, real, true, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
     else k_collide<VS, real, false, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
+    return 4;
+}
+
+template <class VS, typename real, typename S>
+int launch_plain_batch(const BoxArgs<real>* t, int n, unsigned gx, unsigned gy, int unit, cudaStream_t st) {
+    if (n <= 0 || gx == 0 || gy == 0) return 0;
+    const dim3 grid(gx, gy, (unsigned)n);
+    k_stream_density_b<VS, real, S><<<grid, kThreads, 0, st>>>(t);
+    k_created_b<VS, real, S><<<grid, kThreads, 0, st>>>(t);
+    k_wall_b<VS, real><<<grid, kThreads, 0, st>>>(t);
+    if (unit) k_collide_b<VS, real, true, S><<<grid, kThreads, 0, st>>>(t);
+    else k_collide_b<VS, real, false, S><<<grid, kThreads, 0, st>>>(t);
     return 4;
 }
 

@@ -34,7 +34,10 @@ ALL_FIELDS = 0x7F
 
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
            "lbm_fields", "lbm_sync", "lbm_destroy", "lbm_last_error", "lbm_kernel_launches",
-           "lbm_profile", "lbm_timings", "lbm_step_noalloc")
+           "lbm_profile", "lbm_timings", "lbm_step_noalloc",
+           "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_autotune",
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_plan")
+LBM_TUNE_MAX = 32
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -76,6 +79,18 @@ class lbm_timing(C.Structure):
                 ("plain_groups", C.c_longlong), ("bulk_sites", C.c_longlong), ("plain_sites", C.c_longlong)]
 
 
+class lbm_batch_tuning(C.Structure):
+    _fields_ = [("variant", C.c_int), ("zchunk", C.c_int), ("ms_per_step", C.c_double), ("n_tried", C.c_int),
+                ("tried_variant", C.c_int * LBM_TUNE_MAX), ("tried_zchunk", C.c_int * LBM_TUNE_MAX),
+                ("tried_ms", C.c_double * LBM_TUNE_MAX)]
+
+
+class lbm_batch_plan_info(C.Structure):
+    _fields_ = [("n_lattices", C.c_int), ("variant", C.c_int), ("tile_h", C.c_int), ("n_items", C.c_int),
+                ("grid", C.c_int), ("steps_per_graph", C.c_int), ("steps", C.c_longlong),
+                ("launches", C.c_longlong)]
+
+
 _lib = None
 
 
@@ -104,8 +119,23 @@ def lib():
         L.lbm_timings.argtypes = [H, C.POINTER(lbm_timing)]
         L.lbm_step_noalloc.argtypes = [C.POINTER(lbm_config), C.POINTER(lbm_geometry), C.POINTER(lbm_rheology),
                                        C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbm_diag)]
+        L.lbm_batch_create.argtypes = [C.POINTER(H), C.c_int, C.POINTER(H)]
+        L.lbm_batch_step.argtypes = [H, C.c_int]
+        L.lbm_batch_sync.argtypes = [H]
+        L.lbm_batch_set_plan.argtypes = [H, C.c_int, C.POINTER(C.c_int)]
+        L.lbm_batch_autotune.argtypes = [H, C.c_int, C.POINTER(lbm_batch_tuning)]
+        L.lbm_batch_info.argtypes = [H, C.POINTER(lbm_batch_plan_info)]
+        L.lbm_batch_destroy.argtypes = [H]
+        L.lbm_batch_destroy.restype = None
+        L.lbm_batch_last_error.argtypes = [H]
+        L.lbm_batch_last_error.restype = C.c_char_p
+        L.lbm_batch_plan.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.c_longlong]
+        L.lbm_batch_plan.restype = C.c_longlong
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
-                     "lbm_fields", "lbm_sync", "lbm_profile", "lbm_timings", "lbm_step_noalloc"):
+                     "lbm_fields", "lbm_sync", "lbm_profile", "lbm_timings", "lbm_step_noalloc",
+                     "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan",
+                     "lbm_batch_autotune", "lbm_batch_info"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -189,6 +219,67 @@ def lbm_timings(h):
     _check(h, lib().lbm_timings(h, C.byref(t)))
     return dict(bulk_ms=t.bulk_ms, plain_ms=t.plain_ms, bulk_launches=t.bulk_launches,
                 plain_groups=t.plain_groups, bulk_sites=t.bulk_sites, plain_sites=t.plain_sites)
+
+
+def _bcheck(b, st):
+    if st != LBM_OK:
+        raise LBMError(st, lib().lbm_batch_last_error(b).decode())
+    return st
+
+
+def lbm_batch_create(handles):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    b = C.c_void_p()
+    st = lib().lbm_batch_create(arr, len(handles), C.byref(b))
+    if st != LBM_OK:
+        raise LBMError(st, lib().lbm_batch_last_error(None).decode())
+    return b
+
+
+def lbm_batch_step(b, nsteps):
+    return _bcheck(b, lib().lbm_batch_step(b, int(nsteps)))
+
+
+def lbm_batch_sync(b):
+    return _bcheck(b, lib().lbm_batch_sync(b))
+
+
+def lbm_batch_set_plan(b, variant, zchunks):
+    arr = (C.c_int * len(zchunks))(*zchunks)
+    return _bcheck(b, lib().lbm_batch_set_plan(b, int(variant), arr))
+
+
+def lbm_batch_autotune(b, trial_steps):
+    t = lbm_batch_tuning()
+    _bcheck(b, lib().lbm_batch_autotune(b, int(trial_steps), C.byref(t)))
+    n = min(t.n_tried, LBM_TUNE_MAX)
+    return dict(variant=t.variant, zchunk=t.zchunk, ms_per_step=t.ms_per_step,
+                tried=[(t.tried_variant[k], t.tried_zchunk[k], t.tried_ms[k]) for k in range(n)])
+
+
+def lbm_batch_info(b):
+    i = lbm_batch_plan_info()
+    _bcheck(b, lib().lbm_batch_info(b, C.byref(i)))
+    return {k: getattr(i, k) for k, _ in lbm_batch_plan_info._fields_}
+
+
+def lbm_batch_destroy(b):
+    lib().lbm_batch_destroy(b)
+
+
+def lbm_batch_plan(dims, tile_h, zchunks):
+    """Work list of the persistent bulk kernel (host-only): list of
+    (lattice, x0, y0, za, zb) for lattices of sizes dims [(nx, ny, nz), ...]."""
+    n = len(dims)
+    d = (C.c_int * (3 * n))(*[v for t in dims for v in t])
+    z = (C.c_int * n)(*zchunks)
+    cnt = lib().lbm_batch_plan(d, n, int(tile_h), z, None, 0)
+    if cnt < 0:
+        raise LBMError(LBM_EINVAL, "lbm_batch_plan: invalid arguments")
+    out = (C.c_int * (4 * cnt))()
+    lib().lbm_batch_plan(d, n, int(tile_h), z, out, cnt)
+    return [(out[4 * k], out[4 * k + 1] & 0xFFFF, out[4 * k + 1] >> 16, out[4 * k + 2], out[4 * k + 3])
+            for k in range(cnt)]
 
 
 # --------------------------------------------------------------------------
@@ -393,3 +484,40 @@ class Lattice:
 
     def timings(self):
         return lbm_timings(self.h)
+
+
+class Batch:
+    """Many lattices advanced together (see lbm_batch_* in include/lbm.h).
+    The Lattice objects stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        self.b = lbm_batch_create([lat.h for lat in self.lattices])
+
+    def step(self, n):
+        lbm_batch_step(self.b, n)
+
+    def sync(self):
+        lbm_batch_sync(self.b)
+
+    def set_plan(self, variant, zchunks):
+        if isinstance(zchunks, int):
+            zchunks = [zchunks] * len(self.lattices)
+        lbm_batch_set_plan(self.b, variant, zchunks)
+
+    def autotune(self, trial_steps=4):
+        return lbm_batch_autotune(self.b, trial_steps)
+
+    def info(self):
+        return lbm_batch_info(self.b)
+
+    def close(self):
+        if self.b is not None:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
