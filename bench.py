@@ -274,6 +274,13 @@ def run_ours(args):
         lat = None
         torch.cuda.empty_cache()
         sweep = run_sweep(args, local)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        if lat is not None:
+            lat.close()
+            lat = None
+        torch.cuda.empty_cache()
+        serving = run_serving(args, local)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O
@@ -294,7 +301,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (populations %.2f GB)" % (BYTES_PER_SITE[storage] * nsites / 1e9),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "unstable": unstable, "sweep": sweep}
+                "clocks": clk.summary(), "unstable": unstable, "sweep": sweep,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -369,6 +377,97 @@ def run_sweep(args, device):
             "what": "64 print runs 96^3..256x96x96 (seeded parameters), wall time of K steps, host-synchronised"}
 
 
+def serve_requests(n, steps_max, seed=5):
+    """Print-run requests shaped like the downscaled runs: 96x48x48 to 128x64x64,
+    nozzle radius 4-10, power-law n in [0.4, 0.8], extrusion 0.02-0.05, head
+    speed 0.005-0.02 l.u./step, steps uniform in [steps_max / 20, steps_max]."""
+    import numpy as np
+    from paper_2102_02655_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.choice([96, 112, 128]))
+        shape = (nx, nx // 2, nx // 2)
+        wl = I.print_run(shape, float(rng.uniform(4.0, 10.0)), 16, float(rng.uniform(0.005, 0.02)),
+                         float(rng.uniform(0.02, 0.05)), float(rng.uniform(0.4, 0.8)), "f16dev",
+                         head_pos=(nx / 4.0, nx / 4.0))
+        out.append((wl, int(rng.integers(max(1, steps_max // 20), steps_max + 1))))
+    return out
+
+
+def run_serving(args, device):
+    """Poisson arrivals (mean rate args.serve_rate per s) of print-run
+    requests, FP16-deviation storage. Continuous batching (lbm_server_*,
+    admission against an HBM budget) vs the serial plain path (each request
+    alone through lbm_create + lbm_step, first come first served), on the same
+    arrival times: latency from arrival to result on the host, p50/p99, and
+    simulations per hour over the makespan."""
+    import numpy as np
+    import torch
+    from paper_2102_02655_gb300 import lbm
+    reqs = serve_requests(args.serve_n, args.serve_steps)
+    rng = np.random.default_rng(11)
+    arrive = np.cumsum(rng.exponential(1.0 / args.serve_rate, len(reqs)))
+    arrive -= arrive[0]
+    work = sum(wl["shape"][0] * wl["shape"][1] * wl["shape"][2] * s for wl, s in reqs)
+
+    # continuous batching
+    srv = lbm.Server(hbm_budget=int(args.serve_budget_gb * 1e9), storage="f16dev", quantum=args.serve_quantum,
+                     max_active=args.serve_max_active, device=device)
+    lat_b = {}
+    ids = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(lat_b) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrive[nxt] <= now:
+            wl, steps = reqs[nxt]
+            ids[srv.submit(wl["shape"], wl["params"], wl["geom"], wl["rheo"], steps)] = nxt
+            nxt += 1
+        st = srv.stats()
+        if st["waiting"] + st["active"] == 0:
+            time.sleep(max(0.0, min(0.01, arrive[nxt] - now)) if nxt < len(reqs) else 0.0)
+            continue
+        srv.poll()
+        for rid in srv.finished():
+            status, _, diag, _ = srv.result(rid, fields=False)
+            k = ids[rid]
+            lat_b[k] = (time.perf_counter() - t0 - arrive[k], status, diag["unstable"])
+    make_b = time.perf_counter() - t0
+    sst = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+
+    # serial plain path on the same arrival times
+    lat_s = {}
+    t0 = time.perf_counter()
+    for k, (wl, steps) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if arrive[k] > now:
+            time.sleep(arrive[k] - now)
+        lat = lbm.Lattice(wl["shape"], wl["params"], wl["geom"], wl["rheo"], path="fused", device=device)
+        lat.step(steps)
+        d = lat.diag()
+        lat.close()
+        lat_s[k] = (time.perf_counter() - t0 - arrive[k], 0, d["unstable"])
+    make_s = time.perf_counter() - t0
+
+    def pct(d, q):
+        return float(np.percentile([v[0] for v in d.values()], q))
+    return {"requests": len(reqs), "steps_range": [max(1, args.serve_steps // 20), args.serve_steps],
+            "rate_per_s": args.serve_rate, "storage": "f16dev", "budget_gb": args.serve_budget_gb,
+            "batched": {"p50_s": pct(lat_b, 50), "p99_s": pct(lat_b, 99), "makespan_s": make_b,
+                        "sims_per_hour": len(reqs) * 3600.0 / make_b, "mlups": work / make_b / 1e6,
+                        "peak_active": sst["peak_active"], "rounds": sst["rounds"],
+                        "batch_rebuilds": sst["batch_rebuilds"],
+                        "failed": sum(1 for v in lat_b.values() if v[1] != 0 or v[2])},
+            "serial": {"p50_s": pct(lat_s, 50), "p99_s": pct(lat_s, 99), "makespan_s": make_s,
+                       "sims_per_hour": len(reqs) * 3600.0 / make_s, "mlups": work / make_s / 1e6,
+                       "failed": sum(1 for v in lat_s.values() if v[2])},
+            "what": "latency = arrival to result on the host; sims/hour over the makespan; same requests and "
+                    "arrival times for both forms"}
+
+
 def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
     import numpy as np
     import torch
@@ -404,6 +503,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched parameter sweep")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-n", type=int, default=40)
+    ap.add_argument("--serve-steps", type=int, default=4000, help="largest step count of a request")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--serve-quantum", type=int, default=200)
+    ap.add_argument("--serve-max-active", type=int, default=32)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--sweep-n", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--storage", choices=["f64", "f32", "f16dev", "bf16dev"], default=None,

@@ -267,6 +267,12 @@ typedef struct lbm_batch lbm_batch;
  * from lbm_batch_last_error(NULL)), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out);
 
+/* Replace the batch's lattices (same conditions as lbm_batch_create, and the
+ * batch's device and storage), keeping its streams and reusing its step
+ * tables where they are large enough; the plan returns to the default. Waits
+ * for the batch's stream. For continuous batching, where members come and go. */
+lbm_status lbm_batch_reset(lbm_batch* b, lbm_handle* const* lattices, int n);
+
 /* Advance every lattice of the batch by nsteps steps (asynchronous on the
  * batch's own stream, ordered after work already enqueued on each lattice's
  * stream and before work enqueued there later). The fields of the last step
@@ -313,6 +319,81 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * ints (lattice, x0 | y0 << 16, za, zb) to items (may be NULL) and returns
  * the item count, or -1 for invalid arguments. */
 long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap);
+
+/* Device bytes lbm_create allocates for cfg (host-only; -1 if cfg is
+ * invalid): both population buffers (with the 16-bit storage's ink-fraction
+ * arrays), the density and top-velocity arrays, the field planes and the
+ * accumulators. */
+long long lbm_lattice_bytes(const lbm_config* cfg);
+
+/* ---------------------------------------------------------------------------
+ * Serving: print-run simulation requests (ink law, extrusion rate, head
+ * velocity, nozzle size: the parameters of Sec. III) arriving over time.
+ * Requests wait in arrival order; each lbm_server_poll admits the waiting
+ * ones while an active slot is free and their lbm_lattice_bytes fit the HBM
+ * budget, advances all active requests together as one batch (lbm_batch_*)
+ * by min(quantum, the fewest remaining steps), and retires the ones that
+ * reached their step count: their rho_ink, rho_amb, ux, uy, uz are copied to
+ * host memory and their slot is free at once, so the next waiting request
+ * can join in the same call (continuous batching). A retired lattice is kept
+ * in a pool for a later request with the same sizes and model constants
+ * (pooled lattices count against the budget and are freed, oldest first,
+ * when a request needs their memory). A result equals what the
+ * same request computes alone (lbm_create + lbm_step) to rounding.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_server lbm_server;
+typedef struct {
+    unsigned long long hbm_budget;  /* device bytes the active lattices may hold */
+    int device;                     /* CUDA device of every request */
+    int storage;                    /* lbm_storage of every request */
+    int quantum;                    /* steps per poll at most */
+    int max_active;                 /* requests advanced together at most */
+} lbm_server_config;
+typedef struct {
+    double t_submit, t_admit, t_done;  /* seconds since lbm_server_create */
+    long long steps;
+} lbm_server_timing;
+typedef struct {
+    int waiting, active, finished, peak_active;
+    long long bytes_in_use;    /* device bytes of active and pooled lattices */
+    long long rounds, batch_steps, site_steps, batch_rebuilds;
+    long long reused;          /* admissions served by a pooled lattice */
+    int pooled;                /* idle lattices kept for reuse */
+    double clock;              /* seconds since lbm_server_create */
+} lbm_server_counters;
+
+lbm_status lbm_server_create(const lbm_server_config* cfg, lbm_server** out);
+
+/* Queue a request: a D3Q19 print run (z_mode walls, open top) of nsteps >= 1
+ * steps from the print setup's initial state (nozzle filled with ink). The
+ * server sets cfg's device, storage, path (fused), stream and allocator.
+ * Writes the request id to *id. The structs are copied. */
+lbm_status lbm_server_submit(lbm_server* s, const lbm_config* cfg, const lbm_geometry* g, const lbm_rheology* r,
+                             long long nsteps, long long* id);
+
+/* One scheduling round (blocks while the round's steps run on the device).
+ * *n_finished: requests finished in this round. */
+lbm_status lbm_server_poll(lbm_server* s, int* n_finished);
+
+/* Ids of finished, uncollected requests (up to cap written); returns how
+ * many there are. */
+int lbm_server_finished(const lbm_server* s, long long* ids, int cap);
+
+/* Collect a finished request: copies its five field planes (nx*ny*nz values
+ * each, double for LBM_F64 else float; NULL entries skipped) to the host
+ * buffers host_dst[0..4] = rho_ink, rho_amb, ux, uy, uz, its diagnostics and
+ * timing, and forgets it. Returns the request's own status (e.g.
+ * LBM_EUNSTABLE, LBM_ENOMEM if it could never fit the budget), LBM_ESTATE
+ * if it has not finished. */
+lbm_status lbm_server_result(lbm_server* s, long long id, void* const* host_dst, lbm_diag* diag,
+                             lbm_server_timing* timing);
+
+lbm_status lbm_server_stats(const lbm_server* s, lbm_server_counters* out);
+
+/* Release the server, its active lattices and uncollected results. */
+void lbm_server_destroy(lbm_server* s);
+
+const char* lbm_server_last_error(const lbm_server* s);
 
 #ifdef __cplusplus
 }

@@ -1071,7 +1071,8 @@ lbm_status batch_steps(lbm_batch* b, int nsteps) {
             b->box_gy = gy;
             b->exec_valid = false;
         }
-        e = cudaMemcpyAsync(b->d_tab, b->h_tab[buf], b->args_bytes + b->box_bytes, cudaMemcpyHostToDevice, b->stream);
+        const size_t tab_bytes = (size_t)b->G * L * (sizeof(StepArgs<real>) + sizeof(BoxArgs<real>));
+        e = cudaMemcpyAsync(b->d_tab, b->h_tab[buf], tab_bytes, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(b->h_ev[buf], b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_step: table upload");
         b->hbuf ^= 1;
@@ -1159,6 +1160,20 @@ lbm_status batch_usable(lbm_batch* b) {
 
 extern "C" {
 
+long long lbm_lattice_bytes(const lbm_config* cfg) {
+    if (!cfg || cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return -1;
+    if (cfg->velset != LBM_D2Q9 && cfg->velset != LBM_D3Q19) return -1;
+    if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16DEV) return -1;
+    const long long Q = cfg->velset == LBM_D3Q19 ? 19 : 9;
+    const long long plane = (long long)cfg->nx * cfg->ny, N = plane * cfg->nz;
+    const long long es = cfg->storage == LBM_F64 ? 8 : 4;
+    const long long ps = cfg->storage == LBM_F64 ? 8 : (cfg->storage == LBM_F32 ? 4 : 2);
+    const long long fdata = (2 * Q * N * ps + 255) & ~255LL;
+    const long long fbytes = fdata + (ps == 2 ? N * es : 0);
+    const long long rbytes = 2 * (N + 2 * plane) * es, ubytes = 3 * 2 * plane * es;
+    return 2 * (fbytes + rbytes + ubytes) + (long long)kNFields * N * es + kAccN * 8 + 256;
+}
+
 long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap) {
     if (!dims || !zchunk || n < 0 || tile_h < 1) return -1;
     for (int l = 0; l < n; ++l)
@@ -1168,40 +1183,85 @@ long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, 
     return plan_items(dims, n, tile_h, zchunk, items, items ? cap : 0);
 }
 
-lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out) {
-    if (!out) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: out is NULL");
-    *out = nullptr;
-    if (!lattices || n < 1) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: need at least one lattice");
+}  // extern "C"
+
+namespace {
+
+// the members' conditions of lbm_batch_create; *unit: their density-ratio class
+lbm_status batch_check(lbm_batch* b, lbm_handle* const* lattices, int n, int* unit) {
+    if (!lattices || n < 1) return bfail(b, LBM_EINVAL, "lbm_batch: need at least one lattice");
     int unit0 = -1;
     for (int l = 0; l < n; ++l) {
         lbm_handle* h = lattices[l];
-        if (!h) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d is NULL", l);
-        if (h->dead) return bfail(nullptr, LBM_ECUDA, "lbm_batch_create: lattice %d is unusable", l);
+        if (!h) return bfail(b, LBM_EINVAL, "lbm_batch: lattice %d is NULL", l);
+        if (h->dead) return bfail(b, LBM_ECUDA, "lbm_batch: lattice %d is unusable", l);
         if (!h->have_geom || !h->have_rheo)
-            return bfail(nullptr, LBM_ESTATE, "lbm_batch_create: lattice %d has no geometry or rheology", l);
+            return bfail(b, LBM_ESTATE, "lbm_batch: lattice %d has no geometry or rheology", l);
         if (!is_fused(h))
-            return bfail(nullptr, LBM_EINVAL,
-                         "lbm_batch_create: lattice %d is not a fused-path lattice (D3Q19, substrate + open top)", l);
+            return bfail(b, LBM_EINVAL, "lbm_batch: lattice %d is not a fused-path lattice (D3Q19, substrate + open top)",
+                         l);
         if (h->cfg.nx > 65535 || h->cfg.ny > 32767)
-            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d too wide for the work list", l);
+            return bfail(b, LBM_EINVAL, "lbm_batch: lattice %d too wide for the work list", l);
         if (h->cfg.device != lattices[0]->cfg.device || h->cfg.storage != lattices[0]->cfg.storage)
-            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattices must share device and storage");
+            return bfail(b, LBM_EINVAL, "lbm_batch: lattices must share device and storage");
+        if (b && (h->cfg.device != b->device || h->cfg.storage != b->storage))
+            return bfail(b, LBM_EINVAL, "lbm_batch_reset: lattices must keep the batch's device and storage");
         for (int m = 0; m < l; ++m)
-            if (lattices[m] == h) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattice %d given twice", l);
+            if (lattices[m] == h) return bfail(b, LBM_EINVAL, "lbm_batch: lattice %d given twice", l);
         StepArgs<double> p;
         memset(&p, 0, sizeof(p));
         fill_model(h, p);
         if (unit0 < 0) unit0 = p.unit;
-        if (p.unit != unit0)
-            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: lattices must all have density ratio one or none");
+        if (p.unit != unit0) return bfail(b, LBM_EINVAL, "lbm_batch: lattices must all have density ratio one or none");
     }
+    *unit = unit0;
+    return LBM_OK;
+}
+
+// members, per-member events, step tables for n lattices, default plan
+lbm_status batch_members(lbm_batch* b, lbm_handle* const* lattices, int n, int unit) {
+    const size_t old_cap = b->hev.size();
+    b->lat.assign(lattices, lattices + n);
+    b->unit = unit;
+    cudaError_t e = cudaSuccess;
+    while (b->hev.size() < (size_t)n && e == cudaSuccess) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->hev.push_back(ev);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch: events");
+    if (!b->d_tab || (size_t)n > old_cap) {
+        // tables sized for the members (capacity grows, never shrinks)
+        if (b->d_tab) cudaFree(b->d_tab);
+        if (b->d_queue) cudaFree(b->d_queue);
+        for (int k = 0; k < 2; ++k)
+            if (b->h_tab[k]) cudaFreeHost(b->h_tab[k]);
+        b->d_tab = b->h_tab[0] = b->h_tab[1] = nullptr;
+        b->d_queue = nullptr;
+        lbm_status st = batch_dispatch<RunAlloc>(b);
+        if (st != LBM_OK) return st;
+    }
+    // default plan: the single-lattice heuristic's z-chunk for each lattice
+    std::vector<int> zc(n);
+    for (int l = 0; l < n; ++l) zc[l] = lattices[l]->zchunk;
+    b->box_gx = b->box_gy = 0;
+    return batch_dispatch<RunPlan>(b, 0, &zc);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: out is NULL");
+    *out = nullptr;
+    int unit = 1;
+    lbm_status st = batch_check(nullptr, lattices, n, &unit);
+    if (st != LBM_OK) return st;
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: host allocation failed");
-    b->lat.assign(lattices, lattices + n);
     b->device = lattices[0]->cfg.device;
     b->storage = lattices[0]->cfg.storage;
-    b->unit = unit0;
-    b->hev.assign(n, nullptr);
     cudaError_t e = cudaSetDevice(b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
@@ -1209,19 +1269,12 @@ lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
-    for (int l = 0; l < n && e == cudaSuccess; ++l) e = cudaEventCreateWithFlags(&b->hev[l], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         bfail(nullptr, LBM_ECUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
         lbm_batch_destroy(b);
         return LBM_ECUDA;
     }
-    lbm_status st = batch_dispatch<RunAlloc>(b);
-    if (st == LBM_OK) {
-        // default plan: the single-lattice heuristic's z-chunk for each lattice
-        std::vector<int> zc(n);
-        for (int l = 0; l < n; ++l) zc[l] = lattices[l]->zchunk;
-        st = batch_dispatch<RunPlan>(b, 0, &zc);
-    }
+    st = batch_members(b, lattices, n, unit);
     if (st != LBM_OK) {
         snprintf(g_create_error, sizeof(g_create_error), "%s", b->err);
         lbm_batch_destroy(b);
@@ -1229,6 +1282,17 @@ lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out)
     }
     *out = b;
     return LBM_OK;
+}
+
+lbm_status lbm_batch_reset(lbm_batch* b, lbm_handle* const* lattices, int n) {
+    lbm_status st = batch_usable(b);
+    if (st != LBM_OK) return st;
+    int unit = 1;
+    if ((st = batch_check(b, lattices, n, &unit)) != LBM_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->side);
+    if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_reset: sync");
+    return batch_members(b, lattices, n, unit);
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {

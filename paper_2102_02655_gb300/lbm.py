@@ -35,8 +35,10 @@ ALL_FIELDS = 0x7F
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
            "lbm_fields", "lbm_sync", "lbm_destroy", "lbm_last_error", "lbm_kernel_launches",
            "lbm_profile", "lbm_timings", "lbm_step_noalloc",
-           "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_autotune",
-           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_plan")
+           "lbm_batch_create", "lbm_batch_reset", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_autotune",
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_plan",
+           "lbm_lattice_bytes", "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_finished",
+           "lbm_server_result", "lbm_server_stats", "lbm_server_destroy", "lbm_server_last_error")
 LBM_TUNE_MAX = 32
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -91,6 +93,22 @@ class lbm_batch_plan_info(C.Structure):
                 ("launches", C.c_longlong)]
 
 
+class lbm_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_ulonglong), ("device", C.c_int), ("storage", C.c_int), ("quantum", C.c_int),
+                ("max_active", C.c_int)]
+
+
+class lbm_server_timing(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double), ("steps", C.c_longlong)]
+
+
+class lbm_server_counters(C.Structure):
+    _fields_ = [("waiting", C.c_int), ("active", C.c_int), ("finished", C.c_int), ("peak_active", C.c_int),
+                ("bytes_in_use", C.c_longlong), ("rounds", C.c_longlong), ("batch_steps", C.c_longlong),
+                ("site_steps", C.c_longlong), ("batch_rebuilds", C.c_longlong), ("reused", C.c_longlong),
+                ("pooled", C.c_int), ("clock", C.c_double)]
+
+
 _lib = None
 
 
@@ -121,6 +139,7 @@ def lib():
                                        C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbm_diag)]
         L.lbm_batch_create.argtypes = [C.POINTER(H), C.c_int, C.POINTER(H)]
         L.lbm_batch_step.argtypes = [H, C.c_int]
+        L.lbm_batch_reset.argtypes = [H, C.POINTER(H), C.c_int]
         L.lbm_batch_sync.argtypes = [H]
         L.lbm_batch_set_plan.argtypes = [H, C.c_int, C.POINTER(C.c_int)]
         L.lbm_batch_autotune.argtypes = [H, C.c_int, C.POINTER(lbm_batch_tuning)]
@@ -132,9 +151,27 @@ def lib():
         L.lbm_batch_plan.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.c_longlong]
         L.lbm_batch_plan.restype = C.c_longlong
+        L.lbm_lattice_bytes.argtypes = [C.POINTER(lbm_config)]
+        L.lbm_lattice_bytes.restype = C.c_longlong
+        L.lbm_server_create.argtypes = [C.POINTER(lbm_server_config), C.POINTER(H)]
+        L.lbm_server_submit.argtypes = [H, C.POINTER(lbm_config), C.POINTER(lbm_geometry), C.POINTER(lbm_rheology),
+                                        C.c_longlong, C.POINTER(C.c_longlong)]
+        L.lbm_server_poll.argtypes = [H, C.POINTER(C.c_int)]
+        L.lbm_server_finished.argtypes = [H, C.POINTER(C.c_longlong), C.c_int]
+        L.lbm_server_finished.restype = C.c_int
+        L.lbm_server_result.argtypes = [H, C.c_longlong, C.POINTER(C.c_void_p), C.POINTER(lbm_diag),
+                                        C.POINTER(lbm_server_timing)]
+        L.lbm_server_stats.argtypes = [H, C.POINTER(lbm_server_counters)]
+        L.lbm_server_destroy.argtypes = [H]
+        L.lbm_server_destroy.restype = None
+        L.lbm_server_last_error.argtypes = [H]
+        L.lbm_server_last_error.restype = C.c_char_p
+        for name in ("lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_result",
+                     "lbm_server_stats"):
+            getattr(L, name).restype = C.c_int
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fields", "lbm_step",
                      "lbm_fields", "lbm_sync", "lbm_profile", "lbm_timings", "lbm_step_noalloc",
-                     "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan",
+                     "lbm_batch_create", "lbm_batch_reset", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_set_plan",
                      "lbm_batch_autotune", "lbm_batch_info"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -234,6 +271,11 @@ def lbm_batch_create(handles):
     if st != LBM_OK:
         raise LBMError(st, lib().lbm_batch_last_error(None).decode())
     return b
+
+
+def lbm_batch_reset(b, handles):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    return _bcheck(b, lib().lbm_batch_reset(b, arr, len(handles)))
 
 
 def lbm_batch_step(b, nsteps):
@@ -494,6 +536,10 @@ class Batch:
         self.lattices = list(lattices)
         self.b = lbm_batch_create([lat.h for lat in self.lattices])
 
+    def reset(self, lattices):
+        lbm_batch_reset(self.b, [lat.h for lat in lattices])
+        self.lattices = list(lattices)
+
     def step(self, n):
         lbm_batch_step(self.b, n)
 
@@ -521,3 +567,80 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Serving loop over the C ABI (see lbm_server_* in include/lbm.h):
+    submit print-run requests, poll to run scheduling rounds, collect results."""
+
+    def __init__(self, hbm_budget, storage="f32", quantum=100, max_active=32, device=0):
+        cfg = lbm_server_config(int(hbm_budget), int(device),
+                                _STORAGE[storage] if isinstance(storage, str) else int(storage),
+                                int(quantum), int(max_active))
+        self.storage = storage
+        self.s = C.c_void_p()
+        st = lib().lbm_server_create(C.byref(cfg), C.byref(self.s))
+        if st != LBM_OK:
+            raise LBMError(st, lib().lbm_server_last_error(None).decode())
+        self.shapes = {}
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, lib().lbm_server_last_error(self.s).decode())
+
+    def submit(self, shape, params, geom, rheo, nsteps):
+        cfg = make_config(tuple(shape), dict(params, storage=self.storage), path="fused")
+        g = make_geometry(geom)
+        r = make_rheology(rheo)
+        rid = C.c_longlong()
+        self._check(lib().lbm_server_submit(self.s, C.byref(cfg), C.byref(g), C.byref(r), int(nsteps),
+                                            C.byref(rid)))
+        self.shapes[rid.value] = tuple(shape)
+        return rid.value
+
+    def poll(self):
+        n = C.c_int()
+        self._check(lib().lbm_server_poll(self.s, C.byref(n)))
+        return n.value
+
+    def finished(self):
+        n = lib().lbm_server_finished(self.s, None, 0)
+        ids = (C.c_longlong * max(1, n))()
+        lib().lbm_server_finished(self.s, ids, n)
+        return list(ids[:n])
+
+    def result(self, rid, fields=True):
+        """(status, fields dict or None, diag dict, timing dict); forgets the request."""
+        nx, ny, nz = self.shapes.pop(rid)
+        npd = np.float64 if self.storage in ("f64", LBM_F64) else np.float32
+        bufs = [np.empty((nz, ny, nx), dtype=npd) for _ in range(5)] if fields else None
+        ptrs = (C.c_void_p * 5)(*[b.ctypes.data for b in bufs]) if fields else None
+        d = lbm_diag()
+        t = lbm_server_timing()
+        st = lib().lbm_server_result(self.s, int(rid), ptrs, C.byref(d), C.byref(t))
+        out = dict(zip(("rho_ink", "rho_amb", "ux", "uy", "uz"), bufs)) if fields else None
+        diag = dict(mass=list(d.mass), momentum=list(d.momentum), bc_flux=list(d.bc_flux), created=list(d.created),
+                    destroyed=list(d.destroyed), step=d.step, unstable=d.unstable)
+        timing = dict(t_submit=t.t_submit, t_admit=t.t_admit, t_done=t.t_done, steps=t.steps)
+        return st, out, diag, timing
+
+    def stats(self):
+        c = lbm_server_counters()
+        lib().lbm_server_stats(self.s, C.byref(c))
+        return {k: getattr(c, k) for k, _ in lbm_server_counters._fields_}
+
+    def close(self):
+        if self.s is not None:
+            lib().lbm_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lattice_bytes(shape, params):
+    cfg = make_config(tuple(shape), params)
+    return lib().lbm_lattice_bytes(C.byref(cfg))
