@@ -577,9 +577,7 @@ __device__ __forceinline__ real phase_field(const StepArgs<real>& p, real rY, re
     return (aY - aB) / (aY + aB);
 }
 
-// Collision at one fluid site (Eq. 4-20, 29), written over the pairs of
-// opposite directions (2p-1, 2p): even moments take pair sums, odd moments
-// pair differences, and each pair's two outputs share their even part.
+// Collision at one fluid site (Eq. 4-20, 29).
 //   f[0][i]: ink populations, f[1][i]: total deviation d_i (see the storage
 //   note at the top); both replaced by the post-collision values.
 //   kUnit: reference densities equal and phi = w (density ratio one); the
@@ -587,37 +585,127 @@ __device__ __forceinline__ real phase_field(const StepArgs<real>& p, real rY, re
 //   rho_B/rho = 1 - cY and rho^N = 2 cY - 1. Otherwise it returns
 //   (cY, cB, rho^N).
 //   zdist: distance to the substrate (drag zone), < 0 when there is none.
-template <class VS, typename real, bool kUnit, typename Nb>
-__device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q], const Nb& nb, real zdist,
-                                        SiteOut<real>* so) {
+//
+// The regularised collision (Eq. 20) rebuilds every population from the
+// moments, so the step splits in two: moments() takes what the site's own
+// populations after streaming give (ink density, total deviation, momentum,
+// the two non-equilibrium stresses: 17 numbers), collide_out() adds the
+// neighbours' colour fractions and writes the new populations, each pair of
+// opposite directions (2p-1, 2p) sharing its even part. collide() is the two
+// in sequence.
+
+template <typename real>
+struct Moments {
+    real rY, sd;   // ink density, sum of the total deviations
+    real m[3];     // momentum sum_i c_i d_i
+    real PY[6];    // ink non-equilibrium stress (Eq. 20): xx yy zz xy xz yz
+    real PT[6];    // mixture non-equilibrium stress
+};
+
+template <class VS, typename real>
+__device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2][VS::Q], Moments<real>* M) {
     constexpr int Q = VS::Q;
-    constexpr int NP = (Q - 1) / 2;
-    // pair sums and differences
-    real sY[NP], sD[NP], dD[NP];
+    // moments (Eq. 2-3) and the second moments of the ink and of the total
+    // deviation, accumulated direction by direction (17 running sums): ink
+    // density from slot 0, total density and momentum from the deviation slot
+    // (sum_i w_i c_i = 0). The densities are summed in direction order, as
+    // every density of the step is, so that a site's colour fraction is the
+    // same bit for bit wherever it is computed.
+    real rY = 0, sd = 0, mx = 0, my = 0, mz = 0;
+    real a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        sY[q] = f[0][2 * q + 1] + f[0][2 * q + 2];
-        sD[q] = f[1][2 * q + 1] + f[1][2 * q + 2];
-        dD[q] = f[1][2 * q + 1] - f[1][2 * q + 2];
-    }
-    // moments (Eq. 2-3): ink density from slot 0, total density and momentum
-    // from the deviation slot (sum_i w_i c_i = 0)
-    real rY = f[0][0], sd = f[1][0], mx = 0, my = 0, mz = 0;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const int i = 2 * q + 1;
-        rY += sY[q];
-        sd += sD[q];
-        if (VS::c(i, 0)) mx += VS::c(i, 0) > 0 ? dD[q] : -dD[q];
-        if (VS::c(i, 1)) my += VS::c(i, 1) > 0 ? dD[q] : -dD[q];
-        if (VS::c(i, 2)) mz += VS::c(i, 2) > 0 ? dD[q] : -dD[q];
+    for (int i = 0; i < Q; ++i) {
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        const real fy = f[0][i], fd = f[1][i];
+        rY += fy;
+        sd += fd;
+        if (cx) mx += cx > 0 ? fd : -fd;
+        if (cy) my += cy > 0 ? fd : -fd;
+        if (cz) mz += cz > 0 ? fd : -fd;
+        if (cx) { a[0] += fy; b[0] += fd; }
+        if (cy) { a[1] += fy; b[1] += fd; }
+        if (cz) { a[2] += fy; b[2] += fd; }
+        if (cx && cy) { a[3] += (cx == cy) ? fy : -fy; b[3] += (cx == cy) ? fd : -fd; }
+        if (cx && cz) { a[4] += (cx == cz) ? fy : -fy; b[4] += (cx == cz) ? fd : -fd; }
+        if (cy && cz) { a[5] += (cy == cz) ? fy : -fy; b[5] += (cy == cz) ? fd : -fd; }
     }
     const real rho = p.rho_ref + sd;
     const real rB = rho - rY;
     const real irho = qdiv(real(1), rho);
     const real ux = mx * irho, uy = my * irho, uz = mz * irho;
-    const real uu = ux * ux + uy * uy + uz * uz;
+
+    // non-equilibrium stresses (Eq. 20): ink Pi^Y = sum f^Y c c - rY (pfac_Y I + u u),
+    // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
+    real* PY = M->PY;
+    real* PT = M->PT;
+    const real pY = p.pfac[0] * rY;
+    real pT = (rho - p.rho_ref) * real(1.0 / 3.0);
+    if (!p.unit) pT += rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0));
+    PT[0] = b[0] - (pT + rho * ux * ux);
+    PT[1] = b[1] - (pT + rho * uy * uy);
+    PT[2] = b[2] - (pT + rho * uz * uz);
+    PT[3] = b[3] - rho * ux * uy;
+    PT[4] = b[4] - rho * ux * uz;
+    PT[5] = b[5] - rho * uy * uz;
+    PY[0] = a[0] - (pY + rY * ux * ux);
+    PY[1] = a[1] - (pY + rY * uy * uy);
+    PY[2] = a[2] - (pY + rY * uz * uz);
+    PY[3] = a[3] - rY * ux * uy;
+    PY[4] = a[4] - rY * ux * uz;
+    PY[5] = a[5] - rY * uy * uz;
+    if (sizeof(real) < sizeof(double) && rY > real(1e-3) * rho) {
+        // FP32 storage: where the ink carries the rheology, sum its stress in
+        // double (the populations convert exactly, and so does the sum of
+        // two), so that only the storage rounding of f^Y remains, not the
+        // cancellation in the sums
+        double c[6] = {0, 0, 0, 0, 0, 0};
+        double rYd = (double)f[0][0];
+#pragma unroll
+        for (int q = 0; q < (Q - 1) / 2; ++q) {
+            const int i = 2 * q + 1;
+            const double v = (double)f[0][i] + (double)f[0][i + 1];
+            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+            rYd += v;
+            if (cx) c[0] += v;
+            if (cy) c[1] += v;
+            if (cz) c[2] += v;
+            if (cx && cy) c[3] += (cx == cy) ? v : -v;
+            if (cx && cz) c[4] += (cx == cz) ? v : -v;
+            if (cy && cz) c[5] += (cy == cz) ? v : -v;
+        }
+        const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
+        PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
+        PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
+        PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
+        PY[3] = (real)(c[3] - rYd * uxd * uyd);
+        PY[4] = (real)(c[4] - rYd * uxd * uzd);
+        PY[5] = (real)(c[5] - rYd * uyd * uzd);
+    }
+    if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
+    M->rY = rY;
+    M->sd = sd;
+    M->m[0] = mx;
+    M->m[1] = my;
+    M->m[2] = mz;
+}
+
+// The collision from the moments and the neighbours' colour fractions
+// (Eq. 5-17, 20, 29): out(i, fY_i, d_i, cY) receives the post-collision ink
+// population and total deviation of each direction i (cY: the site's ink
+// fraction, for the 16-bit storage reference).
+template <class VS, typename real, bool kUnit, typename Nb, typename Out>
+__device__ __forceinline__ void collide_out(const StepArgs<real>& p, const Moments<real>& M, const Nb& nb, real zdist,
+                                            SiteOut<real>* so, Out&& out) {
+    constexpr int Q = VS::Q;
+    constexpr int NP = (Q - 1) / 2;
+    const real rY = M.rY;
+    const real rho = p.rho_ref + M.sd;
+    const real rB = rho - rY;
+    const real irho = qdiv(real(1), rho);
+    const real ux = M.m[0] * irho, uy = M.m[1] * irho, uz = M.m[2] * irho;
     const real cY0 = rY * irho, cB0 = rB * irho;
+    const real* PY = M.PY;
+    const real* PT = M.PT;
 
     // colour-gradient force (Eq. 11) and grad rho^N by the isotropic stencil
     // (Eq. 12), as pair differences 3 sum_p w_p c_p [chi(x + c_p) - chi(x - c_p)]:
@@ -669,71 +757,10 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     const real gN2 = gN[0] * gN[0] + gN[1] * gN[1] + gN[2] * gN[2];
     const real gNn = qsqrt(gN2);
 
-    // non-equilibrium stresses (Eq. 20): ink Pi^Y = sum f^Y c c - rY (pfac_Y I + u u),
-    // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
-    real PY[6], PT[6];  // xx yy zz xy xz yz
-    {
-        real a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const int i = 2 * q + 1;
-            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-            if (cx) { a[0] += sY[q]; b[0] += sD[q]; }
-            if (cy) { a[1] += sY[q]; b[1] += sD[q]; }
-            if (cz) { a[2] += sY[q]; b[2] += sD[q]; }
-            if (cx && cy) { a[3] += (cx == cy) ? sY[q] : -sY[q]; b[3] += (cx == cy) ? sD[q] : -sD[q]; }
-            if (cx && cz) { a[4] += (cx == cz) ? sY[q] : -sY[q]; b[4] += (cx == cz) ? sD[q] : -sD[q]; }
-            if (cy && cz) { a[5] += (cy == cz) ? sY[q] : -sY[q]; b[5] += (cy == cz) ? sD[q] : -sD[q]; }
-        }
-        const real pY = p.pfac[0] * rY;
-        real pT = (rho - p.rho_ref) * real(1.0 / 3.0);
-        if constexpr (!kUnit) pT += rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0));
-        PT[0] = b[0] - (pT + rho * ux * ux);
-        PT[1] = b[1] - (pT + rho * uy * uy);
-        PT[2] = b[2] - (pT + rho * uz * uz);
-        PT[3] = b[3] - rho * ux * uy;
-        PT[4] = b[4] - rho * ux * uz;
-        PT[5] = b[5] - rho * uy * uz;
-        PY[0] = a[0] - (pY + rY * ux * ux);
-        PY[1] = a[1] - (pY + rY * uy * uy);
-        PY[2] = a[2] - (pY + rY * uz * uz);
-        PY[3] = a[3] - rY * ux * uy;
-        PY[4] = a[4] - rY * ux * uz;
-        PY[5] = a[5] - rY * uy * uz;
-        if (sizeof(real) < sizeof(double) && rY > real(1e-3) * rho) {
-            // FP32 storage: where the ink carries the rheology, sum its stress
-            // in double (the populations convert exactly), so that only the
-            // storage rounding of f^Y remains, not the cancellation in the sums
-            double c[6] = {0, 0, 0, 0, 0, 0};
-            double rYd = (double)f[0][0];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                const int i = 2 * q + 1;
-                const double v = (double)f[0][i] + (double)f[0][i + 1];
-                const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-                rYd += v;
-                if (cx) c[0] += v;
-                if (cy) c[1] += v;
-                if (cz) c[2] += v;
-                if (cx && cy) c[3] += (cx == cy) ? v : -v;
-                if (cx && cz) c[4] += (cx == cz) ? v : -v;
-                if (cy && cz) c[5] += (cy == cz) ? v : -v;
-            }
-            const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
-            PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
-            PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
-            PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
-            PY[3] = (real)(c[3] - rYd * uxd * uyd);
-            PY[4] = (real)(c[4] - rYd * uxd * uzd);
-            PY[5] = (real)(c[5] - rYd * uyd * uzd);
-        }
-        if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
-    }
-
     // local relaxation time: ink viscosity from Eq. 24-25, harmonic mixing
     // by mass fraction (Eq. 17), clamp
     const real S = qsqrt(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
-                          real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
+                         real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
     const real tauY = solve_tau_ink(p, S, rY, rho);
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
     const real inv_nu = qdiv(cY0, nuY) + qdiv(cB0, p.nuB);
@@ -765,8 +792,7 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
         const real w = (real)VS::w(0);
         real e = w * drho - rho * w * vv15 + om45 * w * (-tr3) - pA * (real)VS::B(0);
         if constexpr (!kUnit) e += rY * p.dphi[0][0] + rB * p.dphi[1][0];
-        f[1][0] = e;
-        f[0][0] = cY0 * (w * p.rho_ref + e);
+        out(0, cY0 * (w * p.rho_ref + e), e, cY0);
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -790,10 +816,8 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
         else e0 = rY * p.phi[0][i] + rB * p.phi[1][i];
         const real G = rec * cg * e0;
         const real dp = e + o, dm = e - o;
-        f[1][i] = dp;
-        f[1][i + 1] = dm;
-        f[0][i] = cY0 * (w * p.rho_ref + dp) + G;
-        f[0][i + 1] = cY0 * (w * p.rho_ref + dm) - G;
+        out(i, cY0 * (w * p.rho_ref + dp) + G, dp, cY0);
+        out(i + 1, cY0 * (w * p.rho_ref + dm) - G, dm, cY0);
     }
 
     so->rhoY = rY;
@@ -804,6 +828,17 @@ __device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q
     so->tau = tau;
     so->rn = rn0;
     so->cY = cY0;
+}
+
+template <class VS, typename real, bool kUnit, typename Nb>
+__device__ __forceinline__ void collide(const StepArgs<real>& p, real f[2][VS::Q], const Nb& nb, real zdist,
+                                        SiteOut<real>* so) {
+    Moments<real> M;
+    moments<VS>(p, f, &M);
+    collide_out<VS, real, kUnit>(p, M, nb, zdist, so, [&](int i, real fY, real fD, real) {
+        f[0][i] = fY;
+        f[1][i] = fD;
+    });
 }
 
 // unstable: the total density is not finite and positive (a vanishing

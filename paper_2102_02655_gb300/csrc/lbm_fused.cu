@@ -213,17 +213,41 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 // One tile column (x0, y0) of planes [za, zb) of one lattice; shared memory
 // as laid out by fused_smem. Used by the single-lattice kernel (one column
 // per CTA) and by the persistent batched kernel (a list of columns per CTA).
-template <typename real, typename S, bool kUnit, int TY_>
+// kMom: the own sites wait for their collision as their 17 moments (see
+// moments()) instead of their 38 populations, which takes less than half the
+// shared memory and none of the populations' registers across the plane.
+template <typename real, typename S, bool kUnit, int TY_, bool kMom = false>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
     using T = Tile<TY_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
-    real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][38][NT]
-    Colour<real, kUnit, HS> C{pops + 2 * 38 * NT};  // [4 slots][NV][HS]
-    // substrate prologue scratch [2][SS]: population buffer 1, first written
+    constexpr int NS = kMom ? 17 : 38;              // values staged per site
+    real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][NS][NT]
+    Colour<real, kUnit, HS> C{pops + 2 * NS * NT};  // [4 slots][NV][HS]
+    // substrate prologue scratch [2][SS]: staging buffer 1, first written
     // after the prologue's last read of it
-    real* sub = pops + 38 * NT;
+    real* sub = pops + NS * NT;
+    static_assert(NS * NT >= 2 * SS, "substrate scratch");
+    // the staged values of a site: populations, or moments
+    auto stage = [&](real* b, const real f[2][19]) {
+        if constexpr (kMom) {
+            Moments<real> M;
+            moments<D3Q19>(p, f, &M);
+            b[0] = M.rY;
+            b[NT] = M.sd;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) b[(2 + k) * NT] = M.m[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                b[(5 + k) * NT] = M.PY[k];
+                b[(11 + k) * NT] = M.PT[k];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
+        }
+    };
     (void)TX;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -260,11 +284,18 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             }
             const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
             const bool own = it == 0;
-            real* dst = own && keep ? pops + (zz & 1) * 38 * NT + tid : nullptr;
+            real* dst = own && keep ? pops + (zz & 1) * NS * NT + tid : nullptr;
             real rY, rB;
             if (zz == p.nz - 1) {
-                const TopPull<real> r =
-                    pull_top<S>(p, px, py, dst, NT, own && keep && in_xy && zz < zb && !in_box(p, x, y, zz));
+                const bool led = own && keep && in_xy && zz < zb && !in_box(p, x, y, zz);
+                TopPull<real> r;
+                if constexpr (kMom) {
+                    real ft[2][19];  // one plane in nz: the pulled values go through local memory
+                    r = pull_top<S>(p, px, py, &ft[0][0], 1, led);
+                    if (dst) stage(dst, ft);
+                } else {
+                    r = pull_top<S>(p, px, py, dst, NT, led);
+                }
                 rY = r.rY;
                 rB = r.rB;
                 bc[0] += r.b0;
@@ -272,10 +303,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             } else {
                 real f[2][19];
                 pull_interior<S>(p, px, py, zz, f);
-                if (dst) {
-#pragma unroll
-                    for (int i = 0; i < 38; ++i) dst[i * NT] = f[i / 19][i % 19];
-                }
+                if (dst) stage(dst, f);
                 density(f, p, &rY, &rB);
             }
             if (outer) {
@@ -295,18 +323,34 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     const int hgx = wrapn(x0 - 1 + rx, p.nx), hgy = wrapn(y0 - 1 + ry, p.ny);
     const int hj = ry * HX + rx;
     auto load_interior = [&](int zz) {
-        real f[2][19], h[2][19];
-        pull_interior<S>(p, gx, gy, zz, f);
-        if (has_halo) pull_interior<S>(p, hgx, hgy, zz, h);
-        real* b = pops + (zz & 1) * 38 * NT + tid;
-#pragma unroll
-        for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
         real rY, rB;
-        density(f, p, &rY, &rB);
-        C.put(p, slot_of(zz), hidx, rY, rB);
-        if (has_halo) {
-            density(h, p, &rY, &rB);
-            C.put(p, slot_of(zz), hj, rY, rB);
+        if constexpr (kMom) {
+            // one pull at a time: the register budget of more CTAs per SM
+            // holds one site's 38 values, not two
+            {
+                real f[2][19];
+                pull_interior<S>(p, gx, gy, zz, f);
+                stage(pops + (zz & 1) * NS * NT + tid, f);
+                density(f, p, &rY, &rB);
+                C.put(p, slot_of(zz), hidx, rY, rB);
+            }
+            if (has_halo) {
+                real h[2][19];
+                pull_interior<S>(p, hgx, hgy, zz, h);
+                density(h, p, &rY, &rB);
+                C.put(p, slot_of(zz), hj, rY, rB);
+            }
+        } else {
+            real f[2][19], h[2][19];
+            pull_interior<S>(p, gx, gy, zz, f);
+            if (has_halo) pull_interior<S>(p, hgx, hgy, zz, h);
+            stage(pops + (zz & 1) * NS * NT + tid, f);
+            density(f, p, &rY, &rB);
+            C.put(p, slot_of(zz), hidx, rY, rB);
+            if (has_halo) {
+                density(h, p, &rY, &rB);
+                C.put(p, slot_of(zz), hj, rY, rB);
+            }
         }
     };
 
@@ -348,21 +392,36 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
-            real f[2][19];
-            {
-                const real* b = pops + (z & 1) * 38 * NT + tid;
-#pragma unroll
-                for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
-            }
             // open top: zero normal gradient, the ghost plane above is the top plane
             const int sup = z + 1 < p.nz ? slot_of(z + 1) : slot_of(z);
             SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx};
             SiteOut<real> so;
-            collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
             const int s = z * (int)p.plane + y * p.nx + x;
             const int N = (int)p.N;
+            const real* b = pops + (z & 1) * NS * NT + tid;
+            if constexpr (kMom) {
+                Moments<real> M;
+                M.rY = b[0];
+                M.sd = b[NT];
 #pragma unroll
-            for (int i = 0; i < 19; ++i) pop_put<D3Q19, S>(p, i, s, N, f[0][i], f[1][i], so.cY);
+                for (int k = 0; k < 3; ++k) M.m[k] = b[(2 + k) * NT];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    M.PY[k] = b[(5 + k) * NT];
+                    M.PT[k] = b[(11 + k) * NT];
+                }
+                collide_out<D3Q19, real, kUnit>(p, M, nb, real(z) + real(0.5), &so,
+                                                [&](int i, real fY, real fD, real c) {
+                                                    pop_put<D3Q19, S>(p, i, s, N, fY, fD, c);
+                                                });
+            } else {
+                real f[2][19];
+#pragma unroll
+                for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
+                collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
+#pragma unroll
+                for (int i = 0; i < 19; ++i) pop_put<D3Q19, S>(p, i, s, N, f[0][i], f[1][i], so.cY);
+            }
             ref_put<S>(p, s, so.cY);
             if (z >= p.nz - 2)
                 for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
@@ -399,18 +458,18 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int TY_>
+template <typename real, bool kUnit, int TY_, bool kMom = false>
 constexpr size_t fused_smem() {
     using T = Tile<TY_>;
-    return sizeof(real) * (2 * 38 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
+    return sizeof(real) * (2 * (kMom ? 17 : 38) * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
 __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int za = blockIdx.z * zchunk;
-    fused_column<real, S, kUnit, TY_>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
-                                      min(p.nz, za + zchunk));
+    fused_column<real, S, kUnit, TY_, kMom>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
+                                            min(p.nz, za + zchunk));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -418,7 +477,7 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p,
 // zero at launch), so CTAs that become resident late, behind other kernels,
 // simply take fewer columns. Each lattice's step arguments are copied to
 // shared memory when a CTA's column changes lattice.
-template <typename real, typename S, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
 __global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
     k_fused_batch(const StepArgs<real>* __restrict__ args, const int4* __restrict__ items, int n_items,
                   int* __restrict__ queue) {
@@ -442,78 +501,83 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
             last = it.x;
             __syncthreads();
         }
-        fused_column<real, S, kUnit, TY_>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
+        fused_column<real, S, kUnit, TY_, kMom>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
     }
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     using T = Tile<TY_>;
-    constexpr size_t smem = fused_smem<real, kUnit, TY_>();
+    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom>();
     static_assert(smem <= 227 * 1024, "shared memory of one CTA");
     static unsigned configured = 0;  // one bit per device: the attribute is set once per context
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, S, kUnit, TY_, MINB><<<grid, block, smem, st>>>(p, zchunk);
+    k_fused<real, S, kUnit, TY_, MINB, kMom><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
 int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
                      cudaStream_t st, int* occupancy) {
-    constexpr size_t smem = fused_smem<real, kUnit, TY_>();
+    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom>();
     static unsigned configured = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB, kMom>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         configured |= 1u << dev;
     }
     if (occupancy) {
         *occupancy = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_fused_batch<real, S, kUnit, TY_, MINB>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_fused_batch<real, S, kUnit, TY_, MINB, kMom>,
                                                       Tile<TY_>::NT, smem);
         return 0;
     }
     if (n_items <= 0) return 0;
-    k_fused_batch<real, S, kUnit, TY_, MINB><<<grid, dim3(Tile<TY_>::TX, TY_), smem, st>>>(args, items, n_items,
+    k_fused_batch<real, S, kUnit, TY_, MINB, kMom><<<grid, dim3(Tile<TY_>::TX, TY_), smem, st>>>(args, items, n_items,
                                                                                        queue);
     return 1;
 }
 
-template <typename real, typename S, int TY_, int MINB>
+template <typename real, typename S, int TY_, int MINB, bool kMom = false>
 int batch_variant(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
                   cudaStream_t st, int* occupancy) {
-    return unit ? launch_batch_one<real, S, true, TY_, MINB>(args, items, n_items, queue, grid, st, occupancy)
-                : launch_batch_one<real, S, false, TY_, MINB>(args, items, n_items, queue, grid, st, occupancy);
+    return unit ? launch_batch_one<real, S, true, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy)
+                : launch_batch_one<real, S, false, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy);
 }
 
-template <typename real, typename S, int TY_, int MINB>
+template <typename real, typename S, int TY_, int MINB, bool kMom = false>
 int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, S, true, TY_, MINB>(p, zchunk, st)
-                  : launch_one<real, S, false, TY_, MINB>(p, zchunk, st);
+    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom>(p, zchunk, st)
+                  : launch_one<real, S, false, TY_, MINB, kMom>(p, zchunk, st);
 }
 
 }  // namespace
 
-// Variant 0 (default): 32 x 8 tiles, two CTAs per SM (one in FP64). Variant 1
-// (tuning measurements, CGLBM_FUSED_VARIANT=1): 32 x 16 tiles, one CTA per SM.
+// Variant 0 (default): 32 x 8 tiles, own sites staged as their 17 moments,
+// two CTAs per SM (one in FP64). The others exist for tuning measurements
+// (CGLBM_FUSED_VARIANT): 1 = 32 x 16 tiles with staged populations, one CTA
+// per SM; 2 = 32 x 8 tiles with staged populations (38 per site); 3 = moments
+// at three CTAs per SM (80 registers, which spills).
 template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
-        (void)variant;
-        return launch_variant<real, S, 8, 1>(p, zchunk, st);
+        if (variant == 2) return launch_variant<real, S, 8, 1>(p, zchunk, st);
+        return launch_variant<real, S, 8, 1, true>(p, zchunk, st);
     } else {
         if (variant == 1) return launch_variant<real, S, 16, 1>(p, zchunk, st);
-        return launch_variant<real, S, 8, 2>(p, zchunk, st);
+        if (variant == 2) return launch_variant<real, S, 8, 2>(p, zchunk, st);
+        if (variant == 3) return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
+        return launch_variant<real, S, 8, 2, true>(p, zchunk, st);
     }
 }
 
@@ -524,10 +588,10 @@ int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_item
                        int variant, cudaStream_t st, int* occupancy) {
     if constexpr (sizeof(real) == 8) {
         (void)variant;
-        return batch_variant<real, S, 8, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
+        return batch_variant<real, S, 8, 1, true>(args, items, n_items, queue, grid, unit, st, occupancy);
     } else {
         if (variant == 1) return batch_variant<real, S, 16, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
-        return batch_variant<real, S, 8, 2>(args, items, n_items, queue, grid, unit, st, occupancy);
+        return batch_variant<real, S, 8, 2, true>(args, items, n_items, queue, grid, unit, st, occupancy);
     }
 }
 
