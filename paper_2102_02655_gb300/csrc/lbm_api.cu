@@ -448,9 +448,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->esize = cfg->storage == LBM_F64 ? 8 : 4;
     h->psize = cfg->storage == LBM_F64 ? 8 : (cfg->storage == LBM_F32 ? 4 : 2);
     {
-        // z-planes per CTA of the fused kernel: about six waves of two CTAs
-        // per SM (measured best on the 512x128x128 lattice: 16 planes), at
-        // least 4 planes so the two-plane prologue stays amortised
+        // z-planes per CTA of the fused kernel: 152 x 12 CTAs in all, four
+        // waves of three CTAs per SM (16 and 24 planes measure the same on the
+        // 512x128x128 lattice), at least 4 planes so the two-plane prologue
+        // stays amortised
         const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 7) / 8);
         long long chunks = (152LL * 12 + tiles - 1) / tiles;
         chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));

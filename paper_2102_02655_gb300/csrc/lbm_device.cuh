@@ -602,7 +602,49 @@ struct Moments {
     real PT[6];    // mixture non-equilibrium stress
 };
 
+// FP32 storage: where the ink carries the rheology (rho_Y > 1e-3 rho), its
+// stress is summed in double (the populations convert exactly, and so does
+// the sum of two), so that only the storage rounding of f^Y remains, not the
+// cancellation in the sums. u is the FP32 velocity of the site.
 template <class VS, typename real>
+__device__ __forceinline__ void ink_stress_exact(const StepArgs<real>& p, const real fy[VS::Q], real ux, real uy,
+                                                 real uz, real PY[6]) {
+    constexpr int Q = VS::Q;
+    double c[6] = {0, 0, 0, 0, 0, 0};
+    double rYd = (double)fy[0];
+#pragma unroll
+    for (int q = 0; q < (Q - 1) / 2; ++q) {
+        const int i = 2 * q + 1;
+        const double v = (double)fy[i] + (double)fy[i + 1];
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        rYd += v;
+        if (cx) c[0] += v;
+        if (cy) c[1] += v;
+        if (cz) c[2] += v;
+        if (cx && cy) c[3] += (cx == cy) ? v : -v;
+        if (cx && cz) c[4] += (cx == cz) ? v : -v;
+        if (cy && cz) c[5] += (cy == cz) ? v : -v;
+    }
+    const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
+    PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
+    PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
+    PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
+    PY[3] = (real)(c[3] - rYd * uxd * uyd);
+    PY[4] = (real)(c[4] - rYd * uxd * uzd);
+    PY[5] = (real)(c[5] - rYd * uyd * uzd);
+    if (VS::kPlanar) PY[1] = PY[3] = PY[5] = 0;
+}
+
+// the sites where ink_stress_exact applies
+template <typename real>
+__device__ __forceinline__ bool ink_exact_site(real rY, real rho) {
+    return sizeof(real) < sizeof(double) && rY > real(1e-3) * rho;
+}
+
+// kExact = false leaves PY in FP32 everywhere: the caller applies
+// ink_stress_exact where ink_exact_site holds (the fused kernel, which stages
+// the moments, does so at the collision)
+template <class VS, typename real, bool kExact = true>
 __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2][VS::Q], Moments<real>* M) {
     constexpr int Q = VS::Q;
     // moments (Eq. 2-3) and the second moments of the ink and of the total
@@ -653,34 +695,7 @@ __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2]
     PY[3] = a[3] - rY * ux * uy;
     PY[4] = a[4] - rY * ux * uz;
     PY[5] = a[5] - rY * uy * uz;
-    if (sizeof(real) < sizeof(double) && rY > real(1e-3) * rho) {
-        // FP32 storage: where the ink carries the rheology, sum its stress in
-        // double (the populations convert exactly, and so does the sum of
-        // two), so that only the storage rounding of f^Y remains, not the
-        // cancellation in the sums
-        double c[6] = {0, 0, 0, 0, 0, 0};
-        double rYd = (double)f[0][0];
-#pragma unroll
-        for (int q = 0; q < (Q - 1) / 2; ++q) {
-            const int i = 2 * q + 1;
-            const double v = (double)f[0][i] + (double)f[0][i + 1];
-            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-            rYd += v;
-            if (cx) c[0] += v;
-            if (cy) c[1] += v;
-            if (cz) c[2] += v;
-            if (cx && cy) c[3] += (cx == cy) ? v : -v;
-            if (cx && cz) c[4] += (cx == cz) ? v : -v;
-            if (cy && cz) c[5] += (cy == cz) ? v : -v;
-        }
-        const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
-        PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
-        PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
-        PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
-        PY[3] = (real)(c[3] - rYd * uxd * uyd);
-        PY[4] = (real)(c[4] - rYd * uxd * uzd);
-        PY[5] = (real)(c[5] - rYd * uyd * uzd);
-    }
+    if (kExact && ink_exact_site(rY, rho)) ink_stress_exact<VS>(p, f[0], ux, uy, uz, PY);
     if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
     M->rY = rY;
     M->sd = sd;

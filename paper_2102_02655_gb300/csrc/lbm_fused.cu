@@ -216,7 +216,7 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 // kMom: the own sites wait for their collision as their 17 moments (see
 // moments()) instead of their 38 populations, which takes less than half the
 // shared memory and none of the populations' registers across the plane.
-template <typename real, typename S, bool kUnit, int TY_, bool kMom = false>
+template <typename real, typename S, bool kUnit, int TY_, bool kMom = false, bool kPre = false>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
     using T = Tile<TY_>;
@@ -233,7 +233,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     auto stage = [&](real* b, const real f[2][19]) {
         if constexpr (kMom) {
             Moments<real> M;
-            moments<D3Q19>(p, f, &M);
+            moments<D3Q19, real, false>(p, f, &M);
             b[0] = M.rY;
             b[NT] = M.sd;
 #pragma unroll
@@ -383,13 +383,39 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
 
     double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
     int bad = 0;
+    // kPre: the own site's populations of the plane after next are pulled
+    // into registers before a collision and staged after it, so their load
+    // latency overlaps the collision (the halo's pull stays synchronous)
+    real g[2][19];
+    const auto pre_ok = [&](int zz) { return zz <= zb && zz < p.nz - 1; };
+    if constexpr (kPre) {
+        if (pre_ok(za + 1)) pull_interior<S>(p, gx, gy, za + 1, g);
+    }
     for (int z = za; z < zb; ++z) {
         // plane z + 1 goes to colour slot (z + 1) mod 4 and population buffer
         // (z + 1) & 1: no collision still running (plane z - 1, other threads)
         // reads that slot, and the buffer's previous plane was read by this
         // thread only
-        if (z + 1 < p.nz - 1) load_interior(z + 1);
-        else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
+        if constexpr (kPre) {
+            if (pre_ok(z + 1)) {
+                real rY, rB;
+                stage(pops + ((z + 1) & 1) * NS * NT + tid, g);
+                density(g, p, &rY, &rB);
+                C.put(p, slot_of(z + 1), hidx, rY, rB);
+                if (has_halo) {
+                    real h[2][19];
+                    pull_interior<S>(p, hgx, hgy, z + 1, h);
+                    density(h, p, &rY, &rB);
+                    C.put(p, slot_of(z + 1), hj, rY, rB);
+                }
+                if (pre_ok(z + 2)) pull_interior<S>(p, gx, gy, z + 2, g);
+            } else if (z + 1 == p.nz - 1) {
+                load_plane(z + 1, true, false);
+            }
+        } else {
+            if (z + 1 < p.nz - 1) load_interior(z + 1);
+            else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
+        }
         __syncthreads();
         if (in_xy && !in_box(p, x, y, z)) {
             // open top: zero normal gradient, the ghost plane above is the top plane
@@ -409,6 +435,18 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                 for (int k = 0; k < 6; ++k) {
                     M.PY[k] = b[(5 + k) * NT];
                     M.PT[k] = b[(11 + k) * NT];
+                }
+                {
+                    // the ink's stress in double where it carries the rheology:
+                    // the site's populations pulled again (still in L2)
+                    const real rho = p.rho_ref + M.sd;
+                    if (ink_exact_site(M.rY, rho)) {
+                        const real irho = qdiv(real(1), rho);
+                        real fe[2][19];
+                        if (z < p.nz - 1) pull_interior<S>(p, gx, gy, z, fe);
+                        else pull_top<S>(p, gx, gy, &fe[0][0], 1, false);
+                        ink_stress_exact<D3Q19>(p, fe[0], M.m[0] * irho, M.m[1] * irho, M.m[2] * irho, M.PY);
+                    }
                 }
                 collide_out<D3Q19, real, kUnit>(p, M, nb, real(z) + real(0.5), &so,
                                                 [&](int i, real fY, real fD, real c) {
@@ -464,12 +502,12 @@ constexpr size_t fused_smem() {
     return sizeof(real) * (2 * (kMom ? 17 : 38) * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, bool kPre = false>
 __global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int za = blockIdx.z * zchunk;
-    fused_column<real, S, kUnit, TY_, kMom>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
-                                            min(p.nz, za + zchunk));
+    fused_column<real, S, kUnit, TY_, kMom, kPre>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
+                                                  min(p.nz, za + zchunk));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -505,7 +543,7 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
     }
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, bool kPre = false>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     using T = Tile<TY_>;
     constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom>();
@@ -514,13 +552,13 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom, kPre>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, S, kUnit, TY_, MINB, kMom><<<grid, block, smem, st>>>(p, zchunk);
+    k_fused<real, S, kUnit, TY_, MINB, kMom, kPre><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
@@ -555,29 +593,36 @@ int batch_variant(const StepArgs<real>* args, const int4* items, int n_items, in
                 : launch_batch_one<real, S, false, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy);
 }
 
-template <typename real, typename S, int TY_, int MINB, bool kMom = false>
+template <typename real, typename S, int TY_, int MINB, bool kMom = false, bool kPre = false>
 int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom>(p, zchunk, st)
-                  : launch_one<real, S, false, TY_, MINB, kMom>(p, zchunk, st);
+    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom, kPre>(p, zchunk, st)
+                  : launch_one<real, S, false, TY_, MINB, kMom, kPre>(p, zchunk, st);
 }
 
 }  // namespace
 
 // Variant 0 (default): 32 x 8 tiles, own sites staged as their 17 moments,
-// two CTAs per SM (one in FP64). The others exist for tuning measurements
-// (CGLBM_FUSED_VARIANT): 1 = 32 x 16 tiles with staged populations, one CTA
-// per SM; 2 = 32 x 8 tiles with staged populations (38 per site); 3 = moments
-// at three CTAs per SM (80 registers, which spills).
+// three CTAs per SM (80 registers; one CTA per SM in FP64). The others exist
+// for tuning measurements (CGLBM_FUSED_VARIANT): 1 = 32 x 16 tiles with
+// staged populations, one CTA per SM; 2 = staged populations (38 per site),
+// two CTAs per SM; 3 = moments at two CTAs per SM; 4 = as 3 with the own
+// site's next populations pulled into registers a plane ahead; 5 = moments at
+// four CTAs per SM (64 registers); 6 = as 0 with that register prefetch.
 template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
         if (variant == 2) return launch_variant<real, S, 8, 1>(p, zchunk, st);
         return launch_variant<real, S, 8, 1, true>(p, zchunk, st);
     } else {
-        if (variant == 1) return launch_variant<real, S, 16, 1>(p, zchunk, st);
-        if (variant == 2) return launch_variant<real, S, 8, 2>(p, zchunk, st);
-        if (variant == 3) return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
-        return launch_variant<real, S, 8, 2, true>(p, zchunk, st);
+        switch (variant) {
+        case 1: return launch_variant<real, S, 16, 1>(p, zchunk, st);
+        case 2: return launch_variant<real, S, 8, 2>(p, zchunk, st);
+        case 3: return launch_variant<real, S, 8, 2, true>(p, zchunk, st);
+        case 4: return launch_variant<real, S, 8, 2, true, true>(p, zchunk, st);
+        case 5: return launch_variant<real, S, 8, 4, true>(p, zchunk, st);
+        case 6: return launch_variant<real, S, 8, 3, true, true>(p, zchunk, st);
+        default: return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
+        }
     }
 }
 
@@ -591,7 +636,7 @@ int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_item
         return batch_variant<real, S, 8, 1, true>(args, items, n_items, queue, grid, unit, st, occupancy);
     } else {
         if (variant == 1) return batch_variant<real, S, 16, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
-        return batch_variant<real, S, 8, 2, true>(args, items, n_items, queue, grid, unit, st, occupancy);
+        return batch_variant<real, S, 8, 3, true>(args, items, n_items, queue, grid, unit, st, occupancy);
     }
 }
 
