@@ -236,8 +236,8 @@ lbm_status lbm_timings(struct lbm_handle* h, lbm_timing* out);
  * All calls share the one array and it keeps the last call's contents (the
  * call clears what must start at zero): calls that overlap on the GPU race,
  * so issue them on one stream or wait between them. Returns LBM_EINVAL for
- * invalid arguments or a lattice whose work space (four densities per site
- * plus the top planes' velocities) exceeds the array, about 500k sites in
+ * invalid arguments or a lattice whose work space (four densities per site,
+ * the top planes' velocities and one byte per column) exceeds the array, about 500k sites in
  * FP64 and 1M in FP32, LBM_ECUDA on a CUDA error,
  * LBM_EUNSTABLE (diag requested) if a site's total density was not finite
  * and positive. */

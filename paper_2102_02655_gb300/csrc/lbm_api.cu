@@ -27,6 +27,18 @@ char g_create_error[256] = "";
 
 long long q20(double v) { return (long long)llround(v * kFx); }
 
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The nozzle-box kernels run on a stream of the highest priority: their small
+// grids then take SM slots first as the bulk kernel's CTAs retire, and the box
+// chain ends before the bulk kernel instead of after it.
+cudaError_t create_box_stream(cudaStream_t* st) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(st, cudaStreamNonBlocking, greatest);
+}
+
 long long mod_ll(long long a, long long m) {
     a %= m;
     return a < 0 ? a + m : a;
@@ -62,6 +74,7 @@ struct lbm_handle {
     void* rho[2] = {nullptr, nullptr};
     void* u[2] = {nullptr, nullptr};
     void* fields = nullptr;
+    unsigned char* geo = nullptr;  // per-column nozzle flags (nx * ny bytes)
     double* acc = nullptr;
     int* flags = nullptr;
     int cur = 0;        // f[cur], rho[cur], u[cur] hold the latest state
@@ -219,6 +232,7 @@ void fill_buffers(lbm_handle* h, StepArgs<real>& p, int src) {
     p.u_prev = (const real*)h->u[src];
     p.u_cur = (real*)h->u[dst];
     p.fields = (real*)h->fields;
+    p.geo = h->geo;
     p.acc = h->acc;
     p.flags = h->flags;
     p.write_fields = 0;
@@ -477,7 +491,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         }
         h->own_stream = true;
     }
-    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    e = create_box_stream(&h->side);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -495,7 +509,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         ok = (h->f[b] = dev_alloc(h, fbytes)) && (h->rho[b] = dev_alloc(h, rbytes)) &&
              (h->u[b] = dev_alloc(h, ubytes));
     }
-    ok = ok && (h->fields = dev_alloc(h, fldbytes)) && (h->acc = (double*)dev_alloc(h, kAccN * sizeof(double))) &&
+    ok = ok && (h->geo = (unsigned char*)dev_alloc(h, round256((size_t)h->plane))) &&
+         (h->fields = dev_alloc(h, fldbytes)) && (h->acc = (double*)dev_alloc(h, kAccN * sizeof(double))) &&
          (h->flags = (int*)dev_alloc(h, 256));
     if (!ok) {
         lbm_destroy(h);
@@ -672,6 +687,7 @@ void lbm_destroy(lbm_handle* h) {
         dev_free(h, h->u[b]);
     }
     dev_free(h, h->fields);
+    dev_free(h, h->geo);
     dev_free(h, h->acc);
     dev_free(h, h->flags);
     for (int g = 0; g < 2; ++g)
@@ -743,7 +759,6 @@ lbm_status noalloc_scratch(int dev, unsigned char** out) {
     return LBM_OK;
 }
 
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <class VS, typename real>
 lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void* f_out, void* fields, lbm_diag* diag,
@@ -761,6 +776,7 @@ lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void*
     real* rho_cur = (real*)(scratch + 512 + rbytes);
     real* u_prev = (real*)(scratch + 512 + 2 * rbytes);
     real* u_cur = (real*)(scratch + 512 + 2 * rbytes + ubytes);
+    unsigned char* geo = scratch + 512 + 2 * rbytes + 2 * ubytes;  // nx * ny bytes
     // the accumulators and the flag must start at zero; the density and
     // velocity arrays are written before they are read
     cudaError_t e = cudaMemsetAsync(scratch, 0, 512, st);
@@ -776,6 +792,7 @@ lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void*
     p.flags = flags;
     p.write_fields = fields ? 1 : 0;
     p.box = Region{0, 0, 0, 0, 0, 0};
+    p.geo = geo;
     launch_prev_from_f<VS, real>(p, rho_prev, u_prev, st);
     const Region R = full_region(tmp);
     launch_plain<VS, real, real>(p, R, R, R, st);
@@ -827,7 +844,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry
     const char* a = (const char*)f_in;
     const char* b = (const char*)f_out;
     if (a < b + fbytes && b < a + fbytes) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: f_in and f_out overlap");
-    const size_t need = 512 + 2 * round256(2 * (size_t)(N + 2 * plane) * es) + 2 * round256(6 * (size_t)plane * es);
+    const size_t need = 512 + 2 * round256(2 * (size_t)(N + 2 * plane) * es) + 2 * round256(6 * (size_t)plane * es) +
+                        round256((size_t)plane);
     if (need > (size_t)LBM_NOALLOC_SCRATCH_BYTES)
         return fail(nullptr, LBM_EINVAL,
                     "lbm_step_noalloc: the lattice needs %zu bytes of work space, the static array holds %u", need,
@@ -1062,6 +1080,7 @@ lbm_status batch_steps(lbm_batch* b, int nsteps) {
                     q.R1g = q.R1;
                     if (q.R1g.z0 <= 0) q.R1g.z0 = -1;
                     if (q.R1g.z1 >= nz) q.R1g.z1 = nz + 1;
+                    q.Rg = grow(q.R2, 2, nx, ny, nz);
                     box_grid(q.R2, q.R1g, &gx, &gy);
                 }
             }
@@ -1096,7 +1115,7 @@ lbm_status batch_steps(lbm_batch* b, int nsteps) {
             h->step += g;
             h->cur ^= (g & 1);
         }
-        b->launches += 5LL * g;
+        b->launches += 6LL * g;  // column flags, four box phases, bulk
         b->steps += g;
         remaining -= g;
     }
@@ -1172,7 +1191,7 @@ long long lbm_lattice_bytes(const lbm_config* cfg) {
     const long long fdata = (2 * Q * N * ps + 255) & ~255LL;
     const long long fbytes = fdata + (ps == 2 ? N * es : 0);
     const long long rbytes = 2 * (N + 2 * plane) * es, ubytes = 3 * 2 * plane * es;
-    return 2 * (fbytes + rbytes + ubytes) + (long long)kNFields * N * es + kAccN * 8 + 256;
+    return 2 * (fbytes + rbytes + ubytes) + (long long)kNFields * N * es + kAccN * 8 + 256 + ((plane + 255) & ~255LL);
 }
 
 long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap) {
@@ -1265,7 +1284,7 @@ lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out)
     b->storage = lattices[0]->cfg.storage;
     cudaError_t e = cudaSetDevice(b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = create_box_stream(&b->side);
     for (cudaEvent_t* ev : {&b->fork, &b->join, &b->done, &b->h_ev[0], &b->h_ev[1]})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t0);

@@ -155,6 +155,9 @@ struct __align__(16) StepArgs {
     int* flags;
     int write_fields;
     Region box;            // nozzle box (fused path); wx = 0 when unused
+    // per-column nozzle flags of this step ([y][x], kGeo* bits), written by
+    // k_geo over the columns the boundary kernels query (nozzle runs only)
+    unsigned char* geo;
 };
 
 // ---------------------------------------------------------------------------
@@ -182,9 +185,16 @@ struct Stored<__nv_bfloat16> {
     static constexpr bool kDev = true;
 };
 
+// FP16 values are stored times 2^13: the deviations (|d| < 8) keep clear of
+// FP16's largest value, and the small ones (ink diffusing into the ambient,
+// 1e-6 .. 1e-9) stay above its subnormal range, where rounding of a
+// positive quantity trailing off to zero loses mass. The scaling is exact.
+constexpr float kF16Scale = 8192.0f, kF16Unscale = 1.0f / 8192.0f;
+
 template <typename S, typename real, typename Idx>
 __device__ __forceinline__ real s_get(const void* b, Idx k) {
-    if constexpr (std::is_same<S, __half>::value) return __half2float(static_cast<const __half*>(b)[k]);
+    if constexpr (std::is_same<S, __half>::value)
+        return __half2float(static_cast<const __half*>(b)[k]) * kF16Unscale;
     else if constexpr (std::is_same<S, __nv_bfloat16>::value)
         return __bfloat162float(static_cast<const __nv_bfloat16*>(b)[k]);
     else return static_cast<const real*>(b)[k];
@@ -192,7 +202,7 @@ __device__ __forceinline__ real s_get(const void* b, Idx k) {
 
 template <typename S, typename real, typename Idx>
 __device__ __forceinline__ void s_put(void* b, Idx k, real v) {
-    if constexpr (std::is_same<S, __half>::value) static_cast<__half*>(b)[k] = __float2half_rn(v);
+    if constexpr (std::is_same<S, __half>::value) static_cast<__half*>(b)[k] = __float2half_rn(v * kF16Scale);
     else if constexpr (std::is_same<S, __nv_bfloat16>::value)
         static_cast<__nv_bfloat16*>(b)[k] = __float2bfloat16_rn(v);
     else static_cast<real*>(b)[k] = v;
@@ -271,12 +281,39 @@ __device__ __forceinline__ long long axis_d2(const StepArgs<real>& p, int x, int
     return dx * dx + dy * dy;
 }
 
+// The nozzle is a vertical annulus above the gap, so a column's relation to it
+// does not depend on z: k_geo classifies each queried column once per step
+// (exact fixed-point arithmetic) and the per-site tests read a byte.
+enum {
+    kGeoSolid0 = 1,   // r_in <= r <= r_out at step n-1
+    kGeoSolid1 = 2,   // same at step n
+    kGeoIn0 = 4,      // r < r_in at step n-1 (inlet above the top)
+    kGeoIn1 = 8,      // r < r_in at step n (ink of the initial fill)
+    kGeoClear0 = 16,  // 3/2 clear of the wall's radii at step n-1
+};
+
+template <typename real>
+__device__ __forceinline__ unsigned geo_flags(const StepArgs<real>& p, int x, int y) {
+    const long long d0 = axis_d2(p, x, y, 0), d1 = axis_d2(p, x, y, 1);
+    unsigned g = 0;
+    if (d0 >= p.rin2 && d0 <= p.rout2) g |= kGeoSolid0;
+    if (d1 >= p.rin2 && d1 <= p.rout2) g |= kGeoSolid1;
+    if (d0 < p.rin2) g |= kGeoIn0;
+    if (d1 < p.rin2) g |= kGeoIn1;
+    if (d0 < p.rclear_in2 || d0 > p.rclear_out2) g |= kGeoClear0;
+    return g;
+}
+
+template <typename real>
+__device__ __forceinline__ unsigned geo_at(const StepArgs<real>& p, int x, int y) {
+    return p.geo[y * p.nx + x];
+}
+
 // nozzle wall node (z >= gap, r_in <= r <= r_out) on the geometry of step n-1 (0) or n (1)
 template <typename real>
 __device__ __forceinline__ bool solid_at(const StepArgs<real>& p, int x, int y, int z, int which) {
     if (!p.nozzle || z < p.gap) return false;
-    long long d2 = axis_d2(p, x, y, which);
-    return d2 >= p.rin2 && d2 <= p.rout2;
+    return (geo_at(p, x, y) & (which ? kGeoSolid1 : kGeoSolid0)) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -346,12 +383,12 @@ __device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, i
             return kLinkMoving;
         }
         if (p.nozzle) {
-            const long long d2 = axis_d2(p, sx, sy, 0);
-            if (d2 >= p.rin2 && d2 <= p.rout2) {
+            const unsigned g = geo_at(p, sx, sy);
+            if (g & kGeoSolid0) {
                 uw[0] = p.vn[0]; uw[1] = p.vn[1]; uw[2] = p.vn[2];
                 return kLinkMoving;
             }
-            if (d2 < p.rin2) {  // inlet, Eq. 27
+            if (g & kGeoIn0) {  // inlet, Eq. 27
                 uw[0] = p.uin[0]; uw[1] = p.uin[1]; uw[2] = p.uin[2];
                 return kLinkMoving;
             }
@@ -373,8 +410,7 @@ __device__ __forceinline__ int classify(const StepArgs<real>& p, int x, int y, i
 template <typename real>
 __device__ __forceinline__ bool clear_of_nozzle(const StepArgs<real>& p, int x, int y, int z) {
     if (!p.nozzle || z < p.gap - 1) return true;
-    const long long d2 = axis_d2(p, x, y, 0);
-    return d2 < p.rclear_in2 || d2 > p.rclear_out2;
+    return (geo_at(p, x, y) & kGeoClear0) != 0;
 }
 
 template <class VS, typename S, typename real>

@@ -607,7 +607,8 @@ int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
 // staged populations, one CTA per SM; 2 = staged populations (38 per site),
 // two CTAs per SM; 3 = moments at two CTAs per SM; 4 = as 3 with the own
 // site's next populations pulled into registers a plane ahead; 5 = moments at
-// four CTAs per SM (64 registers); 6 = as 0 with that register prefetch.
+// four CTAs per SM (64 registers); 6 = as 0 with that register prefetch;
+// 7 = moments on 32 x 12 tiles, two CTAs per SM.
 template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
@@ -621,6 +622,7 @@ int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int varia
         case 4: return launch_variant<real, S, 8, 2, true, true>(p, zchunk, st);
         case 5: return launch_variant<real, S, 8, 4, true>(p, zchunk, st);
         case 6: return launch_variant<real, S, 8, 3, true, true>(p, zchunk, st);
+        case 7: return launch_variant<real, S, 12, 2, true>(p, zchunk, st);
         default: return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
         }
     }

@@ -9,6 +9,7 @@
 namespace cglbm {
 
 // Phase-by-phase step over region R (all sites, or the nozzle box):
+//   0. per-column nozzle flags over R grown by four rings (nozzle runs)
 //   1. stream + densities on R grown by two rings, ledger of R
 //   2. created nodes on R grown by one ring
 //   3. fictitious wall densities and ghost planes on R grown by one ring
@@ -42,7 +43,7 @@ int fused_tile_height(int variant, bool fp64);
 template <typename real>
 struct BoxArgs {
     StepArgs<real> p;
-    Region R, R1, R2, R1g;
+    Region R, R1, R2, R1g, Rg;  // Rg: the columns of the nozzle flags (R2 and two more rings)
 };
 template <class VS, typename real, typename S>
 int launch_plain_batch(const BoxArgs<real>* t, int n, unsigned gx, unsigned gy, int unit, cudaStream_t st);

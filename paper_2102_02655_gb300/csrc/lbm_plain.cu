@@ -55,6 +55,45 @@ inline dim3 region_grid(const Region& r) {
     return dim3((unsigned)((cols + kThreads - 1) / kThreads), (unsigned)(r.z1 - r.z0 > 0 ? r.z1 - r.z0 : 1));
 }
 
+// 0. per-column nozzle flags of this step over region G (columns only)
+template <typename real>
+__device__ __forceinline__ void geo_body(const StepArgs<real>& p, const Region& G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.y != 0 || t >= G.wx * G.wy) return;
+    const int j = t / G.wx, i = t - j * G.wx;
+    const int x = wrapn(G.x0 + i, p.nx), y = wrapn(G.y0 + j, p.ny);
+    p.geo[y * p.nx + x] = (unsigned char)geo_flags(p, x, y);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_geo(StepArgs<real> p, Region G) {
+    geo_body(p, G);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads) k_geo_b(const BoxArgs<real>* __restrict__ t) {
+    const BoxArgs<real>& b = t[blockIdx.z];
+    if (b.R.wx == 0) return;
+    geo_body(b.p, b.Rg);
+}
+
+// the columns the boundary kernels query around region R2: two more rings
+// (neighbours, and the wall-density extrapolation two links out)
+__host__ __device__ inline Region geo_region(const Region& R2, int nx, int ny) {
+    Region g = R2;
+    if (R2.wx + 4 >= nx) { g.x0 = 0; g.wx = nx; }
+    else { g.x0 = R2.x0 - 2 < 0 ? R2.x0 - 2 + nx : R2.x0 - 2; g.wx = R2.wx + 4; }
+    if (R2.wy + 4 >= ny) { g.y0 = 0; g.wy = ny; }
+    else { g.y0 = R2.y0 - 2 < 0 ? R2.y0 - 2 + ny : R2.y0 - 2; g.wy = R2.wy + 4; }
+    g.z0 = 0;
+    g.z1 = 1;
+    return g;
+}
+
+inline dim3 geo_grid(const Region& G) {
+    return dim3((unsigned)(((long long)G.wx * G.wy + kThreads - 1) / kThreads), 1);
+}
+
 // 1. stream + densities (post-streaming) of every fluid node of step n-1 in R2
 template <class VS, typename real, typename S>
 __device__ __forceinline__ void stream_density_body(const StepArgs<real>& p, const Region& R2, const Region& R) {
@@ -377,7 +416,7 @@ __global__ void __launch_bounds__(kThreads) k_init(StepArgs<real> p, int staged,
                 u[2] = p.fields[kFUz * p.N + s];
             }
         } else {
-            const bool ink = p.nozzle && z >= p.gap && axis_d2(p, x, y, 1) < p.rin2;
+            const bool ink = p.nozzle && z >= p.gap && (geo_at(p, x, y) & kGeoIn1);
             rY = ink ? p.rho0[0] : real(0);
             rB = ink ? real(0) : p.rho0[1];
         }
@@ -448,8 +487,14 @@ __global__ void __launch_bounds__(kThreads) k_prev_from_f(StepArgs<real> p, real
 
 template <class VS, typename real>
 int launch_prev_from_f(const StepArgs<real>& p, real* rho_prev, real* u_prev, cudaStream_t st) {
+    int n = 0;
+    if (p.nozzle) {
+        const Region G{0, p.nx, 0, p.ny, 0, 1};
+        k_geo<real><<<geo_grid(G), kThreads, 0, st>>>(p, G);
+        n = 1;
+    }
     k_prev_from_f<VS, real><<<blocks_for(p.N), kThreads, 0, st>>>(p, rho_prev, u_prev);
-    return 1;
+    return 1 + n;
 }
 
 template int launch_plain_batch<D3Q19, float, float>(const BoxArgs<float>*, int, unsigned, unsigned, int, cudaStream_t);
@@ -464,6 +509,12 @@ template int launch_prev_from_f<D2Q9, double>(const StepArgs<double>&, double*, 
 template <class VS, typename real, typename S>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st) {
     if (region_sites(R) == 0) return 0;
+    int n = 0;
+    if (p.nozzle) {
+        const Region G = geo_region(R2, p.nx, p.ny);
+        k_geo<real><<<geo_grid(G), kThreads, 0, st>>>(p, G);
+        n = 1;
+    }
     k_stream_density<VS, real, S><<<region_grid(R2), kThreads, 0, st>>>(p, R2, R);
     k_created<VS, real, S><<<region_grid(R1), kThreads, 0, st>>>(p, R1, R);
     Region R1g = R1;
@@ -474,25 +525,32 @@ int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, con
     k_wall<VS, real><<<region_grid(R1g), kThreads, 0, st>>>(p, R1g);
     if (p.unit) k_collide<VS, real, true, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
     else k_collide<VS, real, false, S><<<region_grid(R), kThreads, 0, st>>>(p, R);
-    return 4;
+    return 4 + n;
 }
 
 template <class VS, typename real, typename S>
 int launch_plain_batch(const BoxArgs<real>* t, int n, unsigned gx, unsigned gy, int unit, cudaStream_t st) {
     if (n <= 0 || gx == 0 || gy == 0) return 0;
     const dim3 grid(gx, gy, (unsigned)n);
+    k_geo_b<real><<<dim3(gx, 1, (unsigned)n), kThreads, 0, st>>>(t);
     k_stream_density_b<VS, real, S><<<grid, kThreads, 0, st>>>(t);
     k_created_b<VS, real, S><<<grid, kThreads, 0, st>>>(t);
     k_wall_b<VS, real><<<grid, kThreads, 0, st>>>(t);
     if (unit) k_collide_b<VS, real, true, S><<<grid, kThreads, 0, st>>>(t);
     else k_collide_b<VS, real, false, S><<<grid, kThreads, 0, st>>>(t);
-    return 4;
+    return 5;
 }
 
 template <class VS, typename real, typename S>
 int launch_init(const StepArgs<real>& p, int staged, int have_u, cudaStream_t st) {
+    int n = 0;
+    if (p.nozzle) {
+        const Region G{0, p.nx, 0, p.ny, 0, 1};
+        k_geo<real><<<geo_grid(G), kThreads, 0, st>>>(p, G);
+        n = 1;
+    }
     k_init<VS, real, S><<<blocks_for(p.N), kThreads, 0, st>>>(p, staged, have_u);
-    return 1;
+    return 1 + n;
 }
 
 template int launch_plain<D3Q19, float, float>(const StepArgs<float>&, const Region&, const Region&, const Region&,

@@ -93,7 +93,7 @@ def test_batch_equals_lone_runs(storage):
         _assert_close(_fields(lat), lone[k], "lattice %d" % k, storage)
     info = batch.info()
     assert info["steps"] == steps and info["n_lattices"] == 5
-    assert info["launches"] == 5 * steps
+    assert info["launches"] == 6 * steps  # column flags, four box phases, bulk
     batch.close()
     for lat in lats:
         lat.close()
