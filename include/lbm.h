@@ -288,15 +288,17 @@ lbm_status lbm_batch_sync(lbm_batch* b);
 lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk);
 
 /* Autotuner: times trial_steps real steps of the batch (after one untimed
- * graph capture) for each candidate plan (variant x z-planes per column in
- * 8 .. 128 up to the tallest lattice) and keeps the fastest. The trial steps
- * advance the lattices (every candidate computes the same result). */
-#define LBM_TUNE_MAX 32
+ * graph capture) for each candidate plan (variant x CTAs per SM of the
+ * persistent bulk kernel, all that fit or one fewer, which leaves room for the
+ * box kernels beside it x z-planes per column in 8 .. 128 up to the tallest
+ * lattice) and keeps the fastest. The trial steps advance the lattices (every
+ * candidate computes the same result). */
+#define LBM_TUNE_MAX 40
 typedef struct {
-    int variant, zchunk;      /* chosen plan */
-    double ms_per_step;       /* its time per batch step */
-    int n_tried;              /* candidates timed */
-    int tried_variant[LBM_TUNE_MAX], tried_zchunk[LBM_TUNE_MAX];
+    int variant, zchunk, ctas_per_sm;  /* chosen plan */
+    double ms_per_step;                /* its time per batch step */
+    int n_tried;                       /* candidates timed */
+    int tried_variant[LBM_TUNE_MAX], tried_zchunk[LBM_TUNE_MAX], tried_ctas[LBM_TUNE_MAX];
     double tried_ms[LBM_TUNE_MAX];
 } lbm_batch_tuning;
 lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* out);

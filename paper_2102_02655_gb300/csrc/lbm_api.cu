@@ -894,6 +894,8 @@ struct lbm_batch {
     size_t items_cap = 0;
     int* d_queue = nullptr;  // one work-queue counter per captured step
     int n_items = 0, grid = 0;
+    int occ = 0;          // resident CTAs per SM of the bulk kernel's configuration
+    int ctas_per_sm = 0;  // CTAs per SM the persistent grid uses (0: all of occ)
     unsigned box_gx = 0, box_gy = 0;
     // step tables: [G][L] StepArgs, then [G][L] BoxArgs
     int G = 16;
@@ -988,7 +990,11 @@ lbm_status batch_plan(lbm_batch* b, int variant, const std::vector<int>& zc) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return bcuda(b, e, "cudaDeviceGetAttribute");
     b->n_items = (int)n;
-    b->grid = (int)std::max(1LL, std::min<long long>(n, (long long)std::max(1, occ) * sms));
+    // fewer CTAs per SM than fit leave room for the box kernels beside the
+    // persistent bulk kernel (a tuning choice)
+    b->occ = std::max(1, occ);
+    const int use = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, b->occ) : b->occ;
+    b->grid = (int)std::max(1LL, std::min<long long>(n, (long long)use * sms));
     b->variant = variant;
     b->zchunk = zc;
     b->exec_valid = false;
@@ -1000,7 +1006,7 @@ lbm_status batch_plan(lbm_batch* b, int variant, const std::vector<int>& zc) {
 // before the captured graph needs a larger grid
 void box_grid(const Region& R2, const Region& R1g, unsigned* gx, unsigned* gy) {
     const long long cols = (long long)(R2.wx + 4) * (R2.wy + 4);
-    *gx = std::max(*gx, (unsigned)((cols + 255) / 256));
+    *gx = std::max(*gx, (unsigned)((cols + kBoxThreads - 1) / kBoxThreads));
     *gy = std::max(*gy, (unsigned)std::max(R2.z1 - R2.z0, R1g.z1 - R1g.z0));
 }
 
@@ -1349,11 +1355,22 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* o
     memset(&res, 0, sizeof(res));
     res.ms_per_step = 1e30;
     for (int v = 0; v < nvar; ++v) {
+      // resident CTAs per SM of this variant (the plan records it)
+      b->ctas_per_sm = 0;
+      {
+          std::vector<int> zc(L, chunks[0]);
+          cudaError_t e = cudaStreamSynchronize(b->stream);
+          if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: sync");
+          if ((st = batch_dispatch<RunPlan>(b, v, &zc)) != LBM_OK) return st;
+      }
+      const int occ = b->occ;
+      for (int k = occ; k >= std::max(1, occ - 1); --k) {
         for (int c : chunks) {
             if (c > max_nz && c != chunks[0]) continue;
             std::vector<int> zc(L, c);
             cudaError_t e = cudaStreamSynchronize(b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: sync");
+            b->ctas_per_sm = k;
             if ((st = batch_dispatch<RunPlan>(b, v, &zc)) != LBM_OK) return st;
             // the first call captures the graph; the second is timed
             const int g = std::min(b->G, trial_steps);
@@ -1370,6 +1387,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* o
             if (res.n_tried < LBM_TUNE_MAX) {
                 res.tried_variant[res.n_tried] = v;
                 res.tried_zchunk[res.n_tried] = c;
+                res.tried_ctas[res.n_tried] = k;
                 res.tried_ms[res.n_tried] = per;
             }
             res.n_tried += 1;
@@ -1377,12 +1395,15 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* o
                 res.ms_per_step = per;
                 res.variant = v;
                 res.zchunk = c;
+                res.ctas_per_sm = k;
             }
         }
+      }
     }
     std::vector<int> zc(L, res.zchunk);
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch_autotune: sync");
+    b->ctas_per_sm = res.ctas_per_sm;
     if ((st = batch_dispatch<RunPlan>(b, res.variant, &zc)) != LBM_OK) return st;
     if (out) *out = res;
     return LBM_OK;

@@ -8,6 +8,10 @@
 
 namespace cglbm {
 
+// block size of the phase-by-phase kernels: 128 threads, small enough for a
+// block to run beside the bulk kernel's CTAs on an SM
+constexpr int kBoxThreads = 128;
+
 // Phase-by-phase step over region R (all sites, or the nozzle box):
 //   0. per-column nozzle flags over R grown by four rings (nozzle runs)
 //   1. stream + densities on R grown by two rings, ledger of R

@@ -9,7 +9,7 @@ namespace cglbm {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kBoxThreads;
 
 // Launch shape of a region: blockIdx.x covers the region's columns (32-bit),
 // blockIdx.y its planes. Returns false for threads past the last column or

@@ -39,7 +39,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_set_ink_rheology", "lbm_set_fi
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_plan",
            "lbm_lattice_bytes", "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_finished",
            "lbm_server_result", "lbm_server_stats", "lbm_server_destroy", "lbm_server_last_error")
-LBM_TUNE_MAX = 32
+LBM_TUNE_MAX = 40
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -82,8 +82,9 @@ class lbm_timing(C.Structure):
 
 
 class lbm_batch_tuning(C.Structure):
-    _fields_ = [("variant", C.c_int), ("zchunk", C.c_int), ("ms_per_step", C.c_double), ("n_tried", C.c_int),
-                ("tried_variant", C.c_int * LBM_TUNE_MAX), ("tried_zchunk", C.c_int * LBM_TUNE_MAX),
+    _fields_ = [("variant", C.c_int), ("zchunk", C.c_int), ("ctas_per_sm", C.c_int), ("ms_per_step", C.c_double),
+                ("n_tried", C.c_int), ("tried_variant", C.c_int * LBM_TUNE_MAX),
+                ("tried_zchunk", C.c_int * LBM_TUNE_MAX), ("tried_ctas", C.c_int * LBM_TUNE_MAX),
                 ("tried_ms", C.c_double * LBM_TUNE_MAX)]
 
 
@@ -295,8 +296,9 @@ def lbm_batch_autotune(b, trial_steps):
     t = lbm_batch_tuning()
     _bcheck(b, lib().lbm_batch_autotune(b, int(trial_steps), C.byref(t)))
     n = min(t.n_tried, LBM_TUNE_MAX)
-    return dict(variant=t.variant, zchunk=t.zchunk, ms_per_step=t.ms_per_step,
-                tried=[(t.tried_variant[k], t.tried_zchunk[k], t.tried_ms[k]) for k in range(n)])
+    return dict(variant=t.variant, zchunk=t.zchunk, ctas_per_sm=t.ctas_per_sm, ms_per_step=t.ms_per_step,
+                tried=[(t.tried_variant[k], t.tried_zchunk[k], t.tried_ms[k]) for k in range(n)],
+                tried_ctas=[t.tried_ctas[k] for k in range(n)])
 
 
 def lbm_batch_info(b):

@@ -5,8 +5,9 @@ alone through lbm_step.
 The batched kernels run the same source arithmetic as the single-lattice ones
 but are separate compiled kernels, and the compiler may fuse multiply-adds
 differently in each: the results agree to rounding (1 ulp per step at most),
-so a batch is compared with lone runs at the FP32 parity bar (the 16-bit bar
-for 16-bit storage, where a 1-ulp FP32 difference can flip a 16-bit rounding).
+so a batch is compared with lone runs at a bar a little above that (the
+16-bit bar for 16-bit storage, where a 1-ulp FP32 difference can flip a
+16-bit rounding).
 Within one compiled kernel the work decomposition (z-planes per column) does
 not change a single bit."""
 import numpy as np
@@ -16,7 +17,10 @@ from paper_2102_02655_gb300 import inputs as I
 
 from test_gpu_parity import _lbm, field_errors
 
-BAR = {"f32": 1e-5, "f16dev": 1e-3}
+# FP32: lone and batched kernels differ by an ulp here and there (1e-7 after
+# tens of steps); the bar sits well below what a site left out of a step
+# would cost
+BAR = {"f32": 2e-6, "f16dev": 1e-3}
 LEDGER_BAR = {"f32": 1e-6, "f16dev": 1e-4}
 
 pytestmark = pytest.mark.gpu
