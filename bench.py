@@ -135,7 +135,7 @@ class Clocks:
 
 def _fused_source_sha():
     h = hashlib.sha256()
-    for f in ("lbm_fused.cu", "lbm_device.cuh"):
+    for f in ("lbm_fused_impl.cuh", "lbm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2102_02655_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -35,7 +35,7 @@ typedef enum {
     LBM_ENOMEM = 2,     /* device allocation failed */
     LBM_ECUDA = 3,      /* CUDA runtime error (sticky) */
     LBM_EUNSTABLE = 4,  /* a site's total density was not finite and positive */
-    LBM_ETIMEOUT = 5,   /* a bounded host wait ran out */
+    LBM_ETIMEOUT = 5,   /* a bounded wait ran out (host wait; or, sticky, a kernel's internal wait) */
     LBM_ESTATE = 6      /* call out of order (e.g. lbm_step before geometry and rheology) */
 } lbm_status;
 
@@ -165,7 +165,8 @@ lbm_status lbm_step(struct lbm_handle* h, int nsteps);
 /* Copy the fields selected by mask (LBM_FIELD_*) of the last completed step
  * into dst[0..] (one nx*ny*nz buffer per field, three for LBM_FIELD_U), on the
  * device or host per dst_on_device, and fill *diag if not NULL. Waits for the
- * stream. Returns LBM_EUNSTABLE (after copying) if the unstable flag is set. */
+ * stream. Returns LBM_EUNSTABLE (after copying) if the unstable flag is set, and LBM_ETIMEOUT
+ * (sticky) if a kernel's bounded internal wait ran out (the state is then lost). */
 lbm_status lbm_fields(struct lbm_handle* h, unsigned mask, void* const* dst, int dst_on_device,
                       lbm_diag* diag);
 
@@ -282,8 +283,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Wait for the batch's stream. */
 lbm_status lbm_batch_sync(lbm_batch* b);
 
-/* Set the plan: variant 0 (32 x 8 tile columns) or 1 (32 x 16, FP32 and
- * 16-bit storage only) and, per lattice (host array of n ints), the z-planes
+/* Set the plan: variant 0 (32 x 8 tile columns) or 1 (32 x 16, FP32 storage
+ * only) and, per lattice (host array of n ints), the z-planes
  * each column of the bulk kernel marches. Waits for the batch's stream. */
 lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk);
 

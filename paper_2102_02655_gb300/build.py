@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcglbm.so")
-SOURCES = ["lbm_api.cu", "lbm_plain.cu", "lbm_fused.cu", "lbm_serve.cpp"]
+SOURCES = ["lbm_api.cu", "lbm_plain.cu", "lbm_fused_f32.cu", "lbm_fused_f64.cu", "lbm_fused_f16.cu",
+           "lbm_fused_bf16.cu", "lbm_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -671,7 +671,11 @@ lbm_status lbm_fields(lbm_handle* h, unsigned mask, void* const* dst, int dst_on
         }
         for (int a = 0; a < 3; ++a) diag->momentum[a] = acc[kAccMom + a];
         diag->step = h->step;
-        diag->unstable = flag ? 1 : 0;
+        diag->unstable = (flag & 1) ? 1 : 0;
+    }
+    if (flag & 2) {
+        h->dead = true;  // a kernel left its step unfinished
+        return fail(h, LBM_ETIMEOUT, "lbm_fields: a bounded wait inside a kernel ran out; the state is lost");
     }
     if (flag) return fail(h, LBM_EUNSTABLE, "lbm_fields: a site's total density was not finite and positive");
     return LBM_OK;
@@ -1333,6 +1337,8 @@ lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk) {
     lbm_status st = batch_usable(b);
     if (st != LBM_OK) return st;
     if (variant < 0 || variant > 1) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: variant must be 0 or 1");
+    if (variant == 1 && b->storage != LBM_F32)
+        return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: 32 x 16 tiles (variant 1) need FP32 storage");
     if (!zchunk) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: zchunk is NULL");
     std::vector<int> zc(zchunk, zchunk + b->lat.size());
     for (int v : zc)
@@ -1350,7 +1356,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* o
     int max_nz = 1;
     for (lbm_handle* h : b->lat) max_nz = std::max(max_nz, h->cfg.nz);
     const int chunks[] = {8, 12, 16, 24, 32, 48, 64, 96, 128};
-    const int nvar = b->storage == LBM_F64 ? 1 : 2;
+    const int nvar = b->storage == LBM_F32 ? 2 : 1;  // 32 x 16 tiles: FP32 storage only
     lbm_batch_tuning res;
     memset(&res, 0, sizeof(res));
     res.ms_per_step = 1e30;

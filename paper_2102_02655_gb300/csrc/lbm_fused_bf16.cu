@@ -1,0 +1,12 @@
+// Fused bulk kernels for BF16-deviation storage: the instantiations of
+// lbm_fused_impl.cuh for one storage type, in a translation unit of their own
+// so that the storage types compile in parallel.
+#include "lbm_fused_impl.cuh"
+
+namespace cglbm {
+
+template int launch_fused<float, __nv_bfloat16>(const StepArgs<float>&, int, cudaStream_t, int);
+template int launch_fused_batch<float, __nv_bfloat16>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+                                            cudaStream_t, int*);
+
+}  // namespace cglbm

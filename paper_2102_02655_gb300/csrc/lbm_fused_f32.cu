@@ -1,0 +1,14 @@
+// Fused bulk kernels for FP32 storage: the instantiations of
+// lbm_fused_impl.cuh for one storage type, in a translation unit of their own
+// so that the storage types compile in parallel.
+#include "lbm_fused_impl.cuh"
+
+namespace cglbm {
+
+int fused_tile_height(int variant, bool fp64) { return (!fp64 && variant == 1) ? 16 : 8; }
+
+template int launch_fused<float, float>(const StepArgs<float>&, int, cudaStream_t, int);
+template int launch_fused_batch<float, float>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+                                            cudaStream_t, int*);
+
+}  // namespace cglbm
