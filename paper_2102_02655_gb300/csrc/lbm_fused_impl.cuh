@@ -27,9 +27,9 @@ namespace cglbm {
 namespace {
 
 // Tile geometry: TX x TY sites, one thread each, plus halo rings.
-template <int TY_>
+template <int TY_, int TX_ = 32>
 struct Tile {
-    static constexpr int TX = 32, TY = TY_, NT = TX * TY;
+    static constexpr int TX = TX_, TY = TY_, NT = TX * TY;
     static constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;  // tile + one-site halo
     static constexpr int NRING = HS - NT;                         // halo sites
     static constexpr int SX = TX + 4, SY = TY + 4, SS = SX * SY;  // tile + two rings (substrate ghost)
@@ -142,7 +142,8 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
 __device__ __forceinline__ void warp_add(double* dst, double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+    const unsigned lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;  // tiles narrower than a warp too
+    if (lane == 0 && v != 0.0) atomicAdd(dst, v);
 }
 
 template <typename real>
@@ -219,10 +220,10 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 // kMom: the own sites wait for their collision as their 17 moments (see
 // moments()) instead of their 38 populations, which takes less than half the
 // shared memory and none of the populations' registers across the plane.
-template <typename real, typename S, bool kUnit, int TY_, bool kMom = false>
+template <typename real, typename S, bool kUnit, int TY_, bool kMom = false, int TX_ = 32>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
-    using T = Tile<TY_>;
+    using T = Tile<TY_, TX_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
     constexpr int NS = kMom ? 17 : 38;              // values staged per site
@@ -473,18 +474,18 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int TY_, bool kMom = false>
+template <typename real, bool kUnit, int TY_, bool kMom = false, int TX_ = 32>
 constexpr size_t fused_smem() {
-    using T = Tile<TY_>;
+    using T = Tile<TY_, TX_>;
     return sizeof(real) * (2 * (kMom ? 17 : 38) * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
-__global__ void __launch_bounds__(Tile<TY_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, int TX_ = 32>
+__global__ void __launch_bounds__(Tile<TY_, TX_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int za = blockIdx.z * zchunk;
-    fused_column<real, S, kUnit, TY_, kMom>(p, smraw, blockIdx.x * Tile<TY_>::TX, blockIdx.y * TY_, za,
-                                            min(p.nz, za + zchunk));
+    fused_column<real, S, kUnit, TY_, kMom, TX_>(p, smraw, blockIdx.x * TX_, blockIdx.y * TY_, za,
+                                                 min(p.nz, za + zchunk));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -520,22 +521,22 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
     }
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
+template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, int TX_ = 32>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    using T = Tile<TY_>;
-    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom>();
+    using T = Tile<TY_, TX_>;
+    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom, TX_>();
     static_assert(smem <= 227 * 1024, "shared memory of one CTA");
     static unsigned configured = 0;  // one bit per device: the attribute is set once per context
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom, TX_>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
     dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
-    k_fused<real, S, kUnit, TY_, MINB, kMom><<<grid, block, smem, st>>>(p, zchunk);
+    k_fused<real, S, kUnit, TY_, MINB, kMom, TX_><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
@@ -570,10 +571,10 @@ int batch_variant(const StepArgs<real>* args, const int4* items, int n_items, in
                 : launch_batch_one<real, S, false, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy);
 }
 
-template <typename real, typename S, int TY_, int MINB, bool kMom = false>
+template <typename real, typename S, int TY_, int MINB, bool kMom = false, int TX_ = 32>
 int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom>(p, zchunk, st)
-                  : launch_one<real, S, false, TY_, MINB, kMom>(p, zchunk, st);
+    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom, TX_>(p, zchunk, st)
+                  : launch_one<real, S, false, TY_, MINB, kMom, TX_>(p, zchunk, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -887,8 +888,9 @@ int launch_ws(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
 // for tuning measurements (CGLBM_FUSED_VARIANT): 1 = 32 x 16 tiles with
 // staged populations, one CTA per SM; 2 = staged populations (38 per site),
 // two CTAs per SM; 3 = moments at two CTAs per SM; 7 = warp-specialised
-// (producer and consumer warps), two 512-thread CTAs per SM. 16-bit storage
-// has the default only.
+// (producer and consumer warps), two 512-thread CTAs per SM; 4 = as 0 on
+// 16 x 16 tiles (a 68-site halo ring instead of 84). 16-bit storage has the
+// default only.
 template <typename real, typename S>
 int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
     if constexpr (sizeof(real) == 8) {
@@ -904,6 +906,7 @@ int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int varia
         case 3: return launch_variant<real, S, 8, 2, true>(p, zchunk, st);
         case 7:
             return p.unit ? launch_ws<real, S, true, 2>(p, zchunk, st) : launch_ws<real, S, false, 2>(p, zchunk, st);
+        case 4: return launch_variant<real, S, 16, 3, true, 16>(p, zchunk, st);
         default: return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
         }
     }
