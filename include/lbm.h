@@ -318,7 +318,8 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Host-only helper (no device work): the work list of the persistent bulk
  * kernel for n lattices of sizes dims[3l..3l+2] = (nx, ny, nz), tile height
- * tile_h and z-planes per column zchunk[l]. Writes up to cap items of four
+ * tile_h and at most zchunk[l] z-planes per item (each column's nz planes in
+ * ceil(nz / zchunk[l]) chunks whose lengths differ by at most one). Writes up to cap items of four
  * ints (lattice, x0 | y0 << 16, za, zb) to items (may be NULL) and returns
  * the item count, or -1 for invalid arguments. */
 long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap);

@@ -943,15 +943,15 @@ long long plan_items(const int* dims, int n, int tile_h, const int* zchunk, int*
     long long k = 0;
     for (int l = 0; l < n; ++l) {
         const int nx = dims[3 * l], ny = dims[3 * l + 1], nz = dims[3 * l + 2];
-        const int zc = std::max(1, zchunk[l]);
-        for (int za = 0; za < nz; za += zc)
+        const int nch = z_chunks(nz, std::max(1, zchunk[l]));
+        for (int c = 0; c < nch; ++c)
             for (int y0 = 0; y0 < ny; y0 += tile_h)
                 for (int x0 = 0; x0 < nx; x0 += 32) {
                     if (k < cap && out) {
                         out[4 * k] = l;
                         out[4 * k + 1] = x0 | (y0 << 16);
-                        out[4 * k + 2] = za;
-                        out[4 * k + 3] = std::min(nz, za + zc);
+                        out[4 * k + 2] = z_chunk_begin(nz, nch, c);
+                        out[4 * k + 3] = z_chunk_begin(nz, nch, c + 1);
                     }
                     ++k;
                 }

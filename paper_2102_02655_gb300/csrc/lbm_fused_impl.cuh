@@ -73,18 +73,17 @@ __device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, i
 // links leaving through the open top take the anti-bounce-back value of
 // Eq. 28 with rho_Y = 0 and rho_B = rho_top, the wall velocity extrapolated
 // from the last two planes of the previous step, u_w = 1.5 u(x) - 0.5 u(x + c_i).
-// Stores the 38 populations to
-// dst[i * stride] when dst is set, and returns the densities after streaming
-// and, when ledger, the boundary-link mass change of each component. A rolled
-// loop over a run-time link table: it runs on one plane in nz, so it is kept
-// small rather than fast.
+// Writes the 38 populations to f and returns the densities after streaming
+// and, when ledger, the boundary-link mass change of each component. Every
+// population and velocity is loaded before the boundary rules use them, so
+// the plane costs one memory round trip more than an interior one.
 template <typename real>
 struct TopPull {
     real rY, rB;
     double b0, b1;
 };
 template <typename S, typename real>
-__device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int gx, int gy, real* dst, int stride,
+__device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int gx, int gy, real f[2][19],
                                                   bool ledger) {
     using VS = D3Q19;
     const int zz = p.nz - 1;
@@ -94,46 +93,54 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
     const int rm = (gy == 0 ? ny - 1 : gy - 1) * nx, rp = (gy == ny - 1 ? 0 : gy + 1) * nx;
     const int zoff = zz * pl;
     const int s = zoff + r0 + gx;
-    TopPull<real> r{real(0), real(0), 0.0, 0.0};
-    real sumD = 0;
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const int cx = link<VS>(i, 0), cy = link<VS>(i, 1), cz = link<VS>(i, 2);
-        const int sz = zz - cz;
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        // a link from below the substrate (nz = 1) or from above the top
+        // starts from the site's own opposite population
+        const bool bnd = cz < 0 || (cz > 0 && zz == 0);
+        const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
+        const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
+        const int src = bnd ? s : zoff - cz * pl + sy + sx;
+        const int a = (bnd ? opp(i) : i) * N + src;  // w_i = w_opp(i)
+        f[0][i] = s_get<S, real>(p.fin, a);
+        f[1][i] = s_get<S, real>(p.fin, a + 19 * N);
+        if constexpr (Stored<S>::kDev) f[0][i] += (real)VS::w(i) * p.rho_ref * p.ref_in[src];
+    }
+    real u0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u0[c] = p.u_prev[c * 2 * pl + pl + r0 + gx];
+    TopPull<real> r{real(0), real(0), 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+        if (cz >= 0) continue;  // resting substrate (nz = 1): the bounced-back value as loaded
         const int ib = opp(i);
-        real fY, fD;
-        if (sz < 0) {
-            pop_get<VS, S>(p, p.fin, p.ref_in, ib, s, N, &fY, &fD);
-        } else if (sz >= p.nz) {
-            real uw[3];
-            const int x1 = cx > 0 ? xp : (cx < 0 ? xm : gx), y1 = cy > 0 ? rp : (cy < 0 ? rm : r0);
-            for (int a = 0; a < 3; ++a) {
-                const real u0 = p.u_prev[a * 2 * pl + pl + r0 + gx];
-                uw[a] = p.nz >= 2 ? real(1.5) * u0 - real(0.5) * p.u_prev[a * 2 * pl + y1 + x1] : u0;
-            }
-            const real cu = -(real)(cx * uw[0] + cy * uw[1] + cz * uw[2]);  // c_ib . u_w
-            const real q = real(4.5) * cu * cu - real(1.5) * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
-            const real w = (real)(VS::w(1) * (i <= 6) + VS::w(7) * (i > 6));
-            real oY, oD;
-            pop_get<VS, S>(p, p.fin, p.ref_in, ib, s, N, &oY, &oD);
-            fY = -oY;  // imposed ink density 0
-            fD = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
-            if (ledger) {
-                r.b0 += (double)(fY - oY);
-                r.b1 += (double)((fD - oD) - (fY - oY));
-            }
-        } else {
-            const int sx = cx > 0 ? xm : (cx < 0 ? xp : gx);
-            const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
-            const int src = zoff - cz * pl + sy + sx;
-            pop_get<VS, S>(p, p.fin, p.ref_in, i, src, N, &fY, &fD);
+        const int x1 = cx > 0 ? xp : (cx < 0 ? xm : gx), y1 = cy > 0 ? rp : (cy < 0 ? rm : r0);
+        real uw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const real un = p.u_prev[c * 2 * pl + y1 + x1];  // plane nz - 2 (slot 0 exists for nz = 1 too)
+            uw[c] = p.nz >= 2 ? real(1.5) * u0[c] - real(0.5) * un : u0[c];
         }
-        if (dst) {
-            dst[i * stride] = fY;
-            dst[(19 + i) * stride] = fD;
+        const real cu = -(real)(cx * uw[0] + cy * uw[1] + cz * uw[2]);  // c_ib . u_w
+        const real q = real(4.5) * cu * cu - real(1.5) * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
+        const real w = (real)VS::w(i);
+        const real oY = f[0][i], oD = f[1][i];
+        const real fY = -oY;  // imposed ink density 0
+        const real fD = -oD + real(2) * (p.rho_top * p.dphi[1][ib] + w * (p.rho_top - p.rho_ref) + p.rho_top * w * q);
+        if (ledger) {
+            r.b0 += (double)(fY - oY);
+            r.b1 += (double)((fD - oD) - (fY - oY));
         }
-        r.rY += fY;
-        sumD += fD;
+        f[0][i] = fY;
+        f[1][i] = fD;
+    }
+    real sumD = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        r.rY += f[0][i];
+        sumD += f[1][i];
     }
     r.rB = (p.rho_ref + sumD) - r.rY;
     return r;
@@ -253,6 +260,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         }
     };
     (void)TX;
+    (void)TY;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x = x0 + tx, y = y0 + ty;
@@ -292,14 +300,9 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             real rY, rB;
             if (zz == p.nz - 1) {
                 const bool led = own && keep && in_xy && zz < zb && !in_box(p, x, y, zz);
-                TopPull<real> r;
-                if constexpr (kMom) {
-                    real ft[2][19];  // one plane in nz: the pulled values go through local memory
-                    r = pull_top<S>(p, px, py, &ft[0][0], 1, led);
-                    if (dst) stage(dst, ft);
-                } else {
-                    r = pull_top<S>(p, px, py, dst, NT, led);
-                }
+                real ft[2][19];
+                const TopPull<real> r = pull_top<S>(p, px, py, ft, led);
+                if (dst) stage(dst, ft);
                 rY = r.rY;
                 rB = r.rB;
                 bc[0] += r.b0;
@@ -422,7 +425,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                         const real irho = qdiv(real(1), rho);
                         real fe[2][19];
                         if (z < p.nz - 1) pull_interior<S>(p, gx, gy, z, fe);
-                        else pull_top<S>(p, gx, gy, &fe[0][0], 1, false);
+                        else pull_top<S>(p, gx, gy, fe, false);
                         ink_stress_exact<D3Q19>(p, fe[0], M.m[0] * irho, M.m[1] * irho, M.m[2] * irho, M.PY);
                     }
                 }
@@ -483,9 +486,10 @@ constexpr size_t fused_smem() {
 template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, int TX_ = 32>
 __global__ void __launch_bounds__(Tile<TY_, TX_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int za = blockIdx.z * zchunk;
-    fused_column<real, S, kUnit, TY_, kMom, TX_>(p, smraw, blockIdx.x * TX_, blockIdx.y * TY_, za,
-                                                 min(p.nz, za + zchunk));
+    const int n = z_chunks(p.nz, zchunk);
+    fused_column<real, S, kUnit, TY_, kMom, TX_>(p, smraw, blockIdx.x * TX_, blockIdx.y * TY_,
+                                                 z_chunk_begin(p.nz, n, blockIdx.z),
+                                                 z_chunk_begin(p.nz, n, blockIdx.z + 1));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -535,7 +539,7 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
         configured |= 1u << dev;
     }
     dim3 block(T::TX, T::TY);
-    dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + zchunk - 1) / zchunk);
+    dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, z_chunks(p.nz, zchunk));
     k_fused<real, S, kUnit, TY_, MINB, kMom, TX_><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
@@ -548,8 +552,8 @@ int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items,
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB, kMom>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB, kMom>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured |= 1u << dev;
     }
     if (occupancy) {
@@ -649,8 +653,9 @@ __global__ void __launch_bounds__(512, MINB) k_fused_ws(StepArgs<real> p, int zc
     const int q = producer ? tid - NT : tid;  // the thread's site in the tile
     const int tx = q % TX, ty = q / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * T::TY;
-    const int za = blockIdx.z * zchunk;
-    const int zb = min(p.nz, za + zchunk);
+    const int nch = z_chunks(p.nz, zchunk);
+    const int za = z_chunk_begin(p.nz, nch, blockIdx.z);
+    const int zb = z_chunk_begin(p.nz, nch, blockIdx.z + 1);
     const int zlast = min(zb, p.nz - 1);  // last plane the producers pull
     const int nplanes = zlast - za + 2;   // planes za - 1 .. zlast, index j = zz - za + 1
     const int x = x0 + tx, y = y0 + ty;
@@ -707,9 +712,9 @@ __global__ void __launch_bounds__(512, MINB) k_fused_ws(StepArgs<real> p, int zc
                 real* dst = own ? own_dst : nullptr;
                 real rY, rB;
                 if (zz == p.nz - 1) {
-                    real ft[2][19];  // one plane in nz: the pulled values go through local memory
-                    const TopPull<real> r = pull_top<S>(p, px, py, &ft[0][0], 1,
-                                                        own && dst && in_xy && zz < zb && !in_box(p, x, y, zz));
+                    real ft[2][19];
+                    const TopPull<real> r =
+                        pull_top<S>(p, px, py, ft, own && dst && in_xy && zz < zb && !in_box(p, x, y, zz));
                     if (dst) stage(dst, ft);
                     rY = r.rY;
                     rB = r.rB;
@@ -808,7 +813,7 @@ __global__ void __launch_bounds__(512, MINB) k_fused_ws(StepArgs<real> p, int zc
                         const real irho = qdiv(real(1), rho);
                         real fe[2][19];
                         if (z < p.nz - 1) pull_interior<S>(p, gx, gy, z, fe);
-                        else pull_top<S>(p, gx, gy, &fe[0][0], 1, false);
+                        else pull_top<S>(p, gx, gy, fe, false);
                         ink_stress_exact<D3Q19>(p, fe[0], M.m[0] * irho, M.m[1] * irho, M.m[2] * irho, M.PY);
                     }
                 }
@@ -876,7 +881,7 @@ int launch_ws(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
         cudaFuncSetAttribute(k_fused_ws<real, S, kUnit, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured |= 1u << dev;
     }
-    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, (p.nz + zchunk - 1) / zchunk);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, z_chunks(p.nz, zchunk));
     k_fused_ws<real, S, kUnit, MINB><<<grid, 512, smem, st>>>(p, zchunk);
     return 1;
 }

@@ -12,6 +12,13 @@ namespace cglbm {
 // block to run beside the bulk kernel's CTAs on an SM
 constexpr int kBoxThreads = 128;
 
+// The fused kernels split each tile column's nz planes into
+// ceil(nz / zchunk) chunks of near-equal length (chunk k is
+// [k nz / n, (k + 1) nz / n)), so that the chunk count, and with it the number
+// of waves of CTAs, can be chosen freely without a short last chunk.
+__host__ __device__ inline int z_chunks(int nz, int zchunk) { return (nz + zchunk - 1) / zchunk; }
+__host__ __device__ inline int z_chunk_begin(int nz, int n, int k) { return (int)((long long)k * nz / n); }
+
 // Phase-by-phase step over region R (all sites, or the nozzle box):
 //   0. per-column nozzle flags over R grown by four rings (nozzle runs)
 //   1. stream + densities on R grown by two rings, ledger of R

@@ -31,6 +31,10 @@ def test_work_list_covers_each_site_once(L, tile_h):
         cover[l][za:zb, y0:y0 + tile_h, x0:x0 + 32] += 1
     for c in cover:
         assert np.all(c == 1)
+    # each column's planes in ceil(nz / zchunk) chunks of near-equal length
+    for l, (nx, ny, nz) in enumerate(dims):
+        lens = [zb - za for m, x0, y0, za, zb in items if m == l and x0 == 0 and y0 == 0]
+        assert len(lens) == -(-nz // zc[l]) and max(lens) - min(lens) <= 1
     # lattice-major order: the items of one lattice are contiguous
     ls = [it[0] for it in items]
     assert ls == sorted(ls)

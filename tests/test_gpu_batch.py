@@ -22,6 +22,11 @@ from test_gpu_parity import _lbm, field_errors
 # would cost
 BAR = {"f32": 2e-6, "f16dev": 1e-3}
 LEDGER_BAR = {"f32": 1e-6, "f16dev": 1e-4}
+# a batch that ran other kernel variants (staged populations, moments summed
+# at the collision) for part of its steps follows a different FP32 operation
+# order from the lone default: the two agree to the FP32 parity bar against
+# the oracle, still far below what a site left out of a step costs
+BAR_MIXED = {"f32": 1e-5, "f16dev": 1e-3}
 
 pytestmark = pytest.mark.gpu
 
@@ -64,10 +69,10 @@ def _assert_same(a, b, label):
     assert a[1]["step"] == b[1]["step"]
 
 
-def _assert_close(a, b, label, storage="f32"):
+def _assert_close(a, b, label, storage="f32", bar=BAR):
     """the batch against a lone run: the storage's parity bar"""
     e = field_errors(a[0], b[0], ("rho_ink", "rho_amb", "ux", "uy", "uz", "p", "rhoN"))
-    bad = {k: v for k, v in e.items() if not v <= (2 if k == "rhoN" else 1) * BAR[storage]}
+    bad = {k: v for k, v in e.items() if not v <= (2 if k == "rhoN" else 1) * bar[storage]}
     assert not bad, (label, bad)
     assert np.array_equal(a[0]["solid"], b[0]["solid"]), label
     # ledger terms on the mass scale (small differences of large sums)
@@ -140,7 +145,7 @@ def test_plan_and_autotune_keep_results():
     for k, wl in enumerate(wls):
         lat = _make(lbm, wl, seed=k)
         lat.step(total)
-        _assert_close(got[k], _fields(lat), "lattice %d" % k)
+        _assert_close(got[k], _fields(lat), "lattice %d" % k, bar=BAR_MIXED)
         lat.close()
 
 
