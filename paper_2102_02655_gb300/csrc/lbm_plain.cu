@@ -376,13 +376,21 @@ __device__ __forceinline__ void collide_body(const StepArgs<real>& p, const Regi
     if (bad) atomicOr(p.flags, 1);
 }
 
+// CTAs per SM the collision kernels are compiled for: in FP32 six (at most 85
+// registers), so that the nozzle box's collision runs in one wave
+template <typename real>
+constexpr int collide_min_blocks() {
+    return sizeof(real) == 4 ? 6 : 2;
+}
+
 template <class VS, typename real, bool kUnit, typename S>
-__global__ void __launch_bounds__(kThreads, 2) k_collide(StepArgs<real> p, Region R) {
+__global__ void __launch_bounds__(kThreads, collide_min_blocks<real>()) k_collide(StepArgs<real> p, Region R) {
     collide_body<VS, real, kUnit, S>(p, R);
 }
 
 template <class VS, typename real, bool kUnit, typename S>
-__global__ void __launch_bounds__(kThreads, 2) k_collide_b(const BoxArgs<real>* __restrict__ t) {
+__global__ void __launch_bounds__(kThreads, collide_min_blocks<real>())
+    k_collide_b(const BoxArgs<real>* __restrict__ t) {
     const BoxArgs<real>& b = t[blockIdx.z];
     if (b.R.wx == 0) return;  // no box for this lattice
     collide_body<VS, real, kUnit, S>(b.p, b.R);
