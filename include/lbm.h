@@ -284,8 +284,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 lbm_status lbm_batch_sync(lbm_batch* b);
 
 /* Set the plan: variant 0 (32 x 8 tile columns) or 1 (32 x 16, FP32 storage
- * only) and, per lattice (host array of n ints), the z-planes
- * each column of the bulk kernel marches. Waits for the batch's stream. */
+ * only) and, per lattice (host array of n ints), at most how many z-planes
+ * one CTA of the bulk kernel marches up a column (the column's nz planes are
+ * split into ceil(nz / zchunk) chunks whose lengths differ by at most one).
+ * Waits for the batch's stream. */
 lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk);
 
 /* Autotuner: times trial_steps real steps of the batch (after one untimed
@@ -319,8 +321,9 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Host-only helper (no device work): the work list of the persistent bulk
  * kernel for n lattices of sizes dims[3l..3l+2] = (nx, ny, nz), tile height
  * tile_h and at most zchunk[l] z-planes per item (each column's nz planes in
- * ceil(nz / zchunk[l]) chunks whose lengths differ by at most one). Writes up to cap items of four
- * ints (lattice, x0 | y0 << 16, za, zb) to items (may be NULL) and returns
+ * ceil(nz / zchunk[l]) chunks whose lengths differ by at most one). Writes up
+ * to cap items of four ints (lattice, x0 | y0 << 16, za, zb) to items (may be
+ * NULL) and returns
  * the item count, or -1 for invalid arguments. */
 long long lbm_batch_plan(const int* dims, int n, int tile_h, const int* zchunk, int* items, long long cap);
 
