@@ -299,6 +299,30 @@ def test_fused_equals_plain_f32():
     assert_close(outs[1], outs[0], TOL["f32"], label="fused vs plain f32")
 
 
+def test_fused_zchunk_split_is_bitwise_invariant(monkeypatch):
+    """The fused kernel splits each tile column's planes into ceil(nz / zchunk)
+    chunks of near-equal length; a chunk recomputes the planes below its first
+    one with the same arithmetic, so the fields do not depend on the split
+    (nz = 45: one chunk, three of 15, seven of 6 or 7, twelve of 3 or 4)."""
+    lbm = _lbm()
+    shape = (64, 40, 45)
+    wl = I.print_run(shape, 6.0, 12, 0.02, 0.03, 0.6, "f32", head_pos=(20.0, 20.0))
+    rY, rB = I.nozzle_fill(shape, wl["geom"])
+    rB = I.perturbed_ambient(shape, rB, seed=4)
+    outs = []
+    for zc in (45, 15, 7, 4):
+        monkeypatch.setenv("CGLBM_ZCHUNK", str(zc))
+        lat = lbm.Lattice(shape, wl["params"], wl["geom"], wl["rheo"], path="fused")
+        lat.set_fields(rY, rB)
+        lat.step(25)
+        f = lat.fields()
+        outs.append({k: np.asarray(v).copy() for k, v in f.items() if k != "diag"})
+        lat.close()
+    for o in outs[1:]:
+        for k in outs[0]:
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
 def test_unstable_flag_from_host_injected_nan():
     lbm = _lbm()
     shape = (16, 8, 12)
