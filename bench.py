@@ -134,9 +134,13 @@ class Clocks:
 
 
 def _fused_source_sha():
+    """Key of the committed ncu traffic figure: the fused kernel's sources and
+    its build flags."""
+    from paper_2102_02655_gb300 import build
     h = hashlib.sha256()
     for f in ("lbm_fused_impl.cuh", "lbm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2102_02655_gb300", "csrc", f), "rb").read())
+    h.update(" ".join(build.ARCH + build.FLAGS[:6] + build.FILE_FLAGS["lbm_fused_f32.cu"]).encode())
     return h.hexdigest()[:16]
 
 
