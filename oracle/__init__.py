@@ -28,7 +28,7 @@ class _Params(C.Structure):
                 ("A", C.c_double), ("beta", C.c_double),
                 ("zeta_ink", C.c_double), ("zeta_amb", C.c_double),
                 ("drag_gamma", C.c_double), ("drag_height", C.c_double),
-                ("g", C.c_double * 3)]
+                ("g", C.c_double * 3), ("grad_floor", C.c_double)]
 
 
 class _Geom(C.Structure):
@@ -71,6 +71,8 @@ def lib():
         L.or_fields.argtypes = [C.c_void_p, dp]
         L.or_get_diag.argtypes = [C.c_void_p, C.POINTER(_Diag)]
         L.or_get_populations.argtypes = [C.c_void_p, dp]
+        L.or_get_post_stream.argtypes = [C.c_void_p, dp]
+        L.or_get_densities.argtypes = [C.c_void_p, dp]
         L.or_velset.argtypes = [C.c_int, C.POINTER(C.c_int), dp, dp]
         L.or_phi.restype = C.c_double
         L.or_phi.argtypes = [C.c_int, C.c_double, C.c_int]
@@ -85,6 +87,23 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# |grad rho^N| at or below which Eq. 16's direction is taken as undefined
+# (cos phi_i = 0): 2^8 units of rounding of the arithmetic that computes the
+# gradient. A run compared with a path that computes in FP32 (FP32 or 16-bit
+# storage) takes that path's level; the oracle itself computes in FP64.
+GRAD_FLOOR = {"f64": 2.0 ** -45, "f32": 2.0 ** -16, "f16dev": 2.0 ** -16, "bf16dev": 2.0 ** -16}
+
+
+def grad_floor(params):
+    """The Eq. 16 floor of a parameter dictionary: its "grad_floor" key, else
+    the level of its "storage" arithmetic (FP64 when absent)."""
+    p = params or {}
+    if p.get("grad_floor"):
+        return float(p["grad_floor"])
+    st = p.get("storage", "f64")
+    return GRAD_FLOOR.get(st, GRAD_FLOOR["f64"]) if isinstance(st, str) else GRAD_FLOOR["f64"]
 
 
 DEFAULT_PARAMS = dict(velset=D3Q19, tau_amb=1.0, rho0_ink=1.0, rho0_amb=1.0,
@@ -143,7 +162,8 @@ class Oracle:
         self.shape = (nx, ny, nz)
         self._p = _Params(nx, ny, nz, vs, p["tau_amb"], p["rho0_ink"], p["rho0_amb"],
                           a_ink, a_amb, p["A"], p["beta"], p["zeta_ink"], p["zeta_amb"],
-                          p["drag_gamma"], p["drag_height"], (C.c_double * 3)(*p["body_force"]))
+                          p["drag_gamma"], p["drag_height"], (C.c_double * 3)(*p["body_force"]),
+                          grad_floor(p))
         self.Q = 9 if vs == D2Q9 else 19
         self._h = lib().or_create(C.byref(self._p))
         if not self._h:
@@ -199,6 +219,22 @@ class Oracle:
         out = np.zeros(2 * self.Q * nx * ny * nz)
         lib().or_get_populations(self._h, _dp(out))
         return out.reshape(2, self.Q, nz, ny, nx)
+
+    def post_stream(self):
+        """Populations of the last step after streaming and node creation,
+        before the collision: [2, Q, nz, ny, nx]."""
+        nx, ny, nz = self.shape
+        out = np.zeros(2 * self.Q * nx * ny * nz)
+        lib().or_get_post_stream(self._h, _dp(out))
+        return out.reshape(2, self.Q, nz, ny, nx)
+
+    def densities(self):
+        """Densities the last step's colour gradient read: [2, nz + 2, ny, nx],
+        plane index z + 1 for z = -1 .. nz (ghost and wall planes included)."""
+        nx, ny, nz = self.shape
+        out = np.zeros(2 * (nz + 2) * nx * ny)
+        lib().or_get_densities(self._h, _dp(out))
+        return out.reshape(2, nz + 2, ny, nx)
 
     def diag(self):
         d = _Diag()

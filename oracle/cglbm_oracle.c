@@ -307,24 +307,29 @@ static void collide_site(const or_lattice* L, const double* fin, const double* n
     /* colour-gradient force (Eq. 11) with the isotropic gradient (Eq. 12),
      * and the gradient of the phase field rho^N. rho^N is used by the paper but
      * never defined; reading: the usual colour-gradient phase field
-     * (rho_Y/rho_Y0 - rho_B/rho_B0)/(rho_Y/rho_Y0 + rho_B/rho_B0).
+     * (a_Y - a_B)/(a_Y + a_B), a_k = rho_k/rho_k0.
      * Eq. 12 is evaluated as (1/c_s^2) sum_i w_i [chi(x + c_i) - chi(x)] c_i,
      * equal to the printed form because sum_i w_i c_i = 0, and exactly zero on
-     * a uniform field (the printed form leaves rounding noise there, whose
-     * direction would then drive the full recolouring term). */
+     * a uniform field (the printed form leaves rounding noise there).
+     * The phase-field difference rho^N(x + c_i) - rho^N(x) is written as one
+     * fraction, 2 (a_Y,i a_B,0 - a_B,i a_Y,0) / ((a_Y,i + a_B,i)(a_Y,0 + a_B,0)),
+     * an exact rewriting that keeps its relative precision where the ink
+     * density is tiny: there rho^N = -1 + O(rho_Y) would lose every digit of
+     * the difference, and the direction of Eq. 16 is read from it. */
     double gY[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gN[3] = {0, 0, 0};
     const double cY0 = phY, cB0 = phB;
-    const double rn0 = (rho_k[0] / rY0 - rho_k[1] / rB0) / (rho_k[0] / rY0 + rho_k[1] / rB0);
+    const double aY0 = rho_k[0] / rY0, aB0 = rho_k[1] / rB0;
+    const double rn0 = (aY0 - aB0) / (aY0 + aB0);
     for (int i = 1; i < Q; ++i) {
         double nY = nbr[i], nB = nbr[Q + i];
         double tot = nY + nB;
         double cY = nY / tot, cB = nB / tot;
         double aY = nY / rY0, aB = nB / rB0;
-        double rn = (aY - aB) / (aY + aB);
+        double drn = 2.0 * (aY * aB0 - aB * aY0) / ((aY + aB) * (aY0 + aB0));
         for (int a = 0; a < 3; ++a) {
             gY[a] += L->w[i] * (cY - cY0) * L->c[i][a] / CS2;
             gB[a] += L->w[i] * (cB - cB0) * L->c[i][a] / CS2;
-            gN[a] += L->w[i] * (rn - rn0) * L->c[i][a] / CS2;
+            gN[a] += L->w[i] * drn * L->c[i][a] / CS2;
         }
     }
     double F[3];
@@ -396,17 +401,15 @@ static void collide_site(const or_lattice* L, const double* fin, const double* n
 
     /* recolouring (Eq. 14-16). Both lines use the zero-velocity equilibria
      * sum_k rho_k phi^k_i (Eq. 15 prints u; reading: u = 0 as in Eq. 14).
-     * cos(phi_i) of Eq. 16 has no limit where grad rho^N vanishes inside a
-     * mixture (its direction is then rounding noise, yet the term keeps its
-     * full size). Reading: the denominator is sqrt(|grad rho^N|^2 + eps^2)
-     * with eps = 1e-4, which leaves interfaces (|grad| ~ 0.1-1) unchanged to
-     * 1e-7 and makes the term vanish smoothly with the gradient. */
-    const double geps = 1e-4;
-    const double gden = sqrt(gNn * gNn + geps * geps);
+     * cos(phi_i) is Eq. 16 as printed. It is undefined where grad rho^N = 0;
+     * a computed gradient at or below the rounding level of the arithmetic
+     * (grad_floor) has no meaningful direction either, so there, and only
+     * there, cos(phi_i) = 0. */
+    const int has_dir = gNn > L->p.grad_floor;
     for (int i = 0; i < Q; ++i) {
         double cosp = 0.0;
-        if (i != 0)
-            cosp = (L->c[i][0] * gN[0] + L->c[i][1] * gN[1] + L->c[i][2] * gN[2]) / (L->cnorm[i] * gden);
+        if (i != 0 && has_dir)
+            cosp = (L->c[i][0] * gN[0] + L->c[i][1] * gN[1] + L->c[i][2] * gN[2]) / (L->cnorm[i] * gNn);
         double e0 = rho_k[0] * L->phi[0][i] + rho_k[1] * L->phi[1][i];
         double g = L->p.beta * rho_k[0] * rho_k[1] / (rho * rho) * cosp * e0;
         out[i] = phY * fs[i] + g;
@@ -437,6 +440,7 @@ or_lattice* or_create(const or_params* p)
     or_lattice* L = (or_lattice*)calloc(1, sizeof(or_lattice));
     if (!L) return NULL;
     L->p = *p;
+    if (!(L->p.grad_floor > 0.0)) L->p.grad_floor = 0x1p-45;
     L->nx = p->nx; L->ny = p->ny; L->nz = p->nz;
     L->N = (long)p->nx * p->ny * p->nz;
     L->Q = build_velset(p->velset, L->c, L->w, L->B);
@@ -916,5 +920,17 @@ void or_get_diag(const or_lattice* L, or_diag* d)
 int or_get_populations(const or_lattice* L, double* out)
 {
     memcpy(out, L->fstar, sizeof(double) * 2 * L->Q * L->N);
+    return L->Q;
+}
+
+int or_get_post_stream(const or_lattice* L, double* out)
+{
+    memcpy(out, L->fpost, sizeof(double) * 2 * L->Q * L->N);
+    return L->Q;
+}
+
+int or_get_densities(const or_lattice* L, double* out)
+{
+    memcpy(out, L->rho_all, sizeof(double) * 2 * (L->nz + 2) * L->nx * L->ny);
     return L->Q;
 }

@@ -44,6 +44,10 @@ typedef struct {
     double zeta_ink, zeta_amb;  /* wall affinities, Eq. 18 */
     double drag_gamma, drag_height; /* drag near the substrate, Eq. 29 */
     double g[3];                /* body acceleration (for channel-flow checks) */
+    double grad_floor;          /* |grad rho^N| at or below which cos(phi_i) of Eq. 16 is
+                                   taken as 0 (the 0/0 case): the rounding level of the
+                                   arithmetic that computes the gradient; 0 selects
+                                   2^-45 (2^8 units of FP64 rounding) */
 } or_params;
 
 typedef struct {
@@ -86,6 +90,14 @@ int         or_step(or_lattice* L, int nsteps);
 void        or_fields(const or_lattice* L, double* out);   /* OR_NFIELDS * nx*ny*nz */
 void        or_get_diag(const or_lattice* L, or_diag* d);
 int         or_get_populations(const or_lattice* L, double* out); /* 2*Q*N post-collision */
+/* State inside the last step, for the pin tests: the populations after
+ * streaming and node creation, before the collision (2*Q*N; meaningful at the
+ * fluid nodes of the step), and the densities the colour gradient read
+ * (2 components x (nz+2) planes z = -1..nz x ny x nx: fluid nodes after
+ * streaming, created nodes, the fictitious densities of Eq. 18 on solid nodes
+ * and on the substrate or lid plane, the copied ghost plane of an open top). */
+int         or_get_post_stream(const or_lattice* L, double* out);
+int         or_get_densities(const or_lattice* L, double* out);
 
 /* Unit-level entry points used by the pin tests. */
 int    or_velset(int velset, int* c, double* w, double* B);        /* returns Q */

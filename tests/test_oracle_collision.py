@@ -89,16 +89,20 @@ def test_perturbation_stress_closed_form(vs):
 
 
 @pytest.mark.parametrize("vs", [O.D2Q9, O.D3Q19])
-def test_recolouring_closed_form(vs):
+@pytest.mark.parametrize("gscale", [1.0, 1e-3, 1e-9])
+def test_recolouring_closed_form(vs, gscale):
     """Recolouring (Eq. 14-16) leaves the total f* unchanged and moves ink
     momentum along +grad rhoN by exactly beta (rhoY rhoB / rho) kappa n, with
     kappa = sum_i w_i c_ix^2/|c_i| (phi = w at density ratio one) and
-    n = grad rhoN / sqrt(|grad rhoN|^2 + eps^2)."""
+    n = grad rhoN / |grad rhoN|: cos(phi_i) of Eq. 16 as printed, at full size
+    for any gradient above the rounding floor (here down to 1e-9 of the
+    interface scale)."""
     rng = np.random.default_rng(4)
     beta = 0.6
     L0 = _lattice(vs, beta=0.0)
     L1 = _lattice(vs, beta=beta)
-    c, w, B, fin, nbr, g = _state(vs, rng)
+    g0 = np.array([0.03, 0.02, -0.04]) if vs == O.D3Q19 else np.array([0.03, 0.0, -0.04])
+    c, w, B, fin, nbr, g = _state(vs, rng, grad=g0 * gscale)
     o0, _ = L0.collide_one(fin, nbr)
     o1, _ = L1.collide_one(fin, nbr)
     assert np.allclose(o1.sum(0), o0.sum(0), rtol=0, atol=2e-15)
@@ -107,10 +111,16 @@ def test_recolouring_closed_form(vs):
     cn = np.sqrt((c * c).sum(1))
     kappa = sum(w[i] * c[i, 0] ** 2 / cn[i] for i in range(1, len(w)))
     assert kappa == pytest.approx((1 + np.sqrt(2)) / 9 if vs == O.D3Q19 else (4 + np.sqrt(2)) / 18, rel=1e-15)
-    # direction with the regularised norm sqrt(|g|^2 + eps^2), eps = 1e-4
-    n = g / np.sqrt(g @ g + 1e-8)
+    n = g / np.linalg.norm(g)
     shift = ((o1[0] - o0[0])[:, None] * c).sum(0)
-    assert np.allclose(shift, beta * rY * rB / rho * kappa * n, rtol=0, atol=2e-15)
+    # the neighbour densities carry the gradient to ~1e-16 absolute, so its
+    # direction is known to ~1e-16 / |grad|
+    tol = 2e-15 + 4e-16 / (np.linalg.norm(g) / 0.054)
+    assert np.allclose(shift, beta * rY * rB / rho * kappa * n, rtol=0, atol=tol)
+    # and each direction's recolouring term is beta rhoY rhoB/rho^2 cos(phi_i) rho w_i
+    cosp = np.zeros(len(w))
+    cosp[1:] = (c[1:] @ g) / (cn[1:] * np.linalg.norm(g))
+    assert np.allclose(o1[0] - o0[0], beta * rY * rB / rho ** 2 * cosp * rho * w, rtol=0, atol=tol)
 
 
 @pytest.mark.parametrize("vs", [O.D2Q9, O.D3Q19])
@@ -222,15 +232,55 @@ def test_cross_reduces_to_newtonian_and_power_law():
         assert g1 == pytest.approx(g2, rel=1e-4)
 
 
-def test_recolouring_vanishes_with_the_gradient():
-    """At a mixed site whose colour gradient vanishes (a symmetric point) the
-    recolouring must not act in the direction of rounding noise: with the
-    regularised cos(phi) it is bounded by |grad|/eps."""
+def test_recolouring_direction_floor():
+    """Eq. 16 has no value where grad rhoN = 0 (0/0). A computed gradient at or
+    below the rounding level of the arithmetic (the floor, 2^8 units of
+    rounding: 2^-45 for FP64, 2^-16 for a path computing in FP32) has no
+    meaningful direction either: there, and only there, cos(phi_i) = 0 and the
+    recolouring leaves f^Y = (rho_Y/rho) f*. Just above the floor it acts at
+    full size."""
     rng = np.random.default_rng(9)
+    for floor in (2.0 ** -45, 2.0 ** -16):
+        L0 = _lattice(O.D3Q19, beta=0.0, grad_floor=floor)
+        L1 = _lattice(O.D3Q19, beta=0.7, grad_floor=floor)
+        for gmag, acts in ((0.0, False), (1e-17, False), (0.5 * floor, False), (2.0 * floor, True)):
+            c, w, B, fin, nbr, g = _state(O.D3Q19, rng, grad=np.array([gmag, 0.0, 0.0]))
+            o0, a0 = L0.collide_one(fin, nbr)
+            o1, a1 = L1.collide_one(fin, nbr)
+            d = np.abs(o1 - o0).max()
+            if acts:
+                # the recolouring term's size: beta rhoY rhoB / rho^2 * rho w_i
+                rY, rB = fin[0].sum(), fin[1].sum()
+                assert d == pytest.approx(0.7 * rY * rB / (rY + rB) / 18, rel=0.05)
+            else:
+                assert d == 0.0
+
+
+def test_default_floor_is_fp64_rounding_level():
+    assert O.grad_floor({}) == 2.0 ** -45
+    assert O.grad_floor({"storage": "f32"}) == 2.0 ** -16
+    assert O.grad_floor({"storage": "f16dev", "grad_floor": 1e-3}) == 1e-3
+
+
+@pytest.mark.parametrize("cy", [1e-13, 1e-8])
+def test_gradient_keeps_relative_precision_in_the_ink_tail(cy):
+    """Far in the ambient the ink fraction is tiny and rho^N = -1 + 2 c_Y; its
+    gradient (Eq. 12) must still come out with the relative precision of the
+    ink densities, since the direction of Eq. 16 is read from it there. With
+    c_Y(x + c_i) = cy (1 + g.c_i) the gradient is 2 cy g exactly (Eq. 12 is
+    exact for linear fields), and the recolouring direction is g/|g|."""
+    L = _lattice(O.D3Q19, beta=0.7)
+    c, w, B = O.velset(O.D3Q19)
+    g = np.array([0.3, -0.2, 0.4])
+    cyn = cy * (1 + c @ g)
+    nbr = np.stack([cyn, 1 - cyn])
+    u = np.zeros(3)
+    fin = np.stack([cy * w, (1 - cy) * w])
+    out, aux = L.collide_one(fin, nbr)
+    assert aux[1] == pytest.approx(2 * cy * np.linalg.norm(g), rel=1e-9)
+    # the ink's recolouring momentum points along +g to the same precision
     L0 = _lattice(O.D3Q19, beta=0.0)
-    L1 = _lattice(O.D3Q19, beta=0.7)
-    for gmag in (0.0, 1e-17, 1e-15):
-        c, w, B, fin, nbr, g = _state(O.D3Q19, rng, grad=np.array([gmag, 0.0, 0.0]))
-        o0, _ = L0.collide_one(fin, nbr)
-        o1, _ = L1.collide_one(fin, nbr)
-        assert np.abs(o1 - o0).max() <= 1e-10
+    o0, _ = L0.collide_one(fin, nbr)
+    shift = ((out[0] - o0[0])[:, None] * c).sum(0)
+    n = shift / np.linalg.norm(shift)
+    assert np.allclose(n, g / np.linalg.norm(g), rtol=0, atol=1e-9)
