@@ -563,6 +563,9 @@ int or_set_geometry(or_lattice* L, const or_geom* g)
     if (!L || !g) return 1;
     if (g->nozzle && g->z_mode != OR_Z_WALLS) return 1;
     if (g->nozzle && (g->gap < 1 || g->gap >= L->nz || !(g->r_inner > 0.0) || !(g->wall_thickness > 0.0))) return 1;
+    /* the fixed-point distances below are squared in 64 bits: exact for
+     * lattice sides up to 4000 and radii up to 2000 */
+    if (g->nozzle && (L->nx > 4000 || L->ny > 4000 || !(g->r_inner + g->wall_thickness <= 2000.0))) return 1;
     L->g = *g;
     L->have_geom = 1;
     L->step = 0;
