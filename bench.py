@@ -134,11 +134,11 @@ class Clocks:
 
 
 def _fused_source_sha():
-    """Key of the committed ncu traffic figure: the fused kernel's sources and
-    its build flags."""
+    """Key of the committed ncu traffic figure: every source of the FP32 fused
+    kernel's translation unit and its build flags."""
     from paper_2102_02655_gb300 import build
     h = hashlib.sha256()
-    for f in ("lbm_fused_impl.cuh", "lbm_device.cuh"):
+    for f in ("lbm_fused_f32.cu", "lbm_fused_impl.cuh", "lbm_launch.h", "lbm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2102_02655_gb300", "csrc", f), "rb").read())
     h.update(" ".join(build.ARCH + build.FLAGS[:6] + build.FILE_FLAGS["lbm_fused_f32.cu"]).encode())
     return h.hexdigest()[:16]
@@ -227,7 +227,9 @@ def run_ours(args):
     def max_over_ranks(v):
         return replica_max(v, ws, "cuda")
 
-    # warm-up
+    # untimed spin-up: the extruded ink thread forms before anything is
+    # timed (a step costs more once ink has left the nozzle), then warm-up
+    lat.step(args.spinup)
     lat.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -263,8 +265,21 @@ def run_ours(args):
             "kernel": "k_fused", "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bps * bulk_sites_launch,
             "kernel_ms_per_launch": bulk_ms_launch,
-            "kernel_share_of_step": tm["bulk_ms"] / max(1e-9, tm["bulk_ms"] + tm["plain_ms"]),
+            # the bulk kernel's own duration over the step's wall time (the
+            # nozzle-box kernels run beside it on a second stream)
+            "kernel_share_of_step": bulk_ms_launch / (ms / args.steps),
             "box_kernels_ms_per_step": tm["plain_ms"] / max(1, tm["plain_groups"])}
+
+    # optional: MLUPS over a long run, in windows, from the fresh nozzle fill
+    trace = None
+    if args.mlups_trace > 0:
+        trace = run_trace(args, wl, rY, rB, lat)
+
+    # config 2's range of ink laws (n = 0.4, 0.6, 0.8), each from its own
+    # spun-up state, same lattice and timing
+    points = None
+    if not args.no_points:
+        points = run_points(args, wl, rY, rB, local, lat)
 
     # end to end through the C ABI with pinned host buffers: upload the
     # initial fields, K steps, read back densities, velocity and diagnostics
@@ -303,13 +318,73 @@ def run_ours(args):
                            "path": "fused bulk kernel + phase-by-phase nozzle box",
                            "nozzle": "r 10, gap 20, head 0.01 l.u./step, power-law n 0.6, extrusion 0.02",
                            "l2": "inputs larger than L2 (populations %.2f GB)" % (BYTES_PER_SITE[storage] * nsites / 1e9),
+                           "spinup_steps": args.spinup,
                            "parallelism": "replicas" if ws > 1 else "single"},
+                "ink_law_points": points,
+                "mlups_trace": trace,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "unstable": unstable, "sweep": sweep,
                 "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_trace(args, wl, rY, rB, lat0, window=500):
+    """MLUPS of each window of `window` steps over args.mlups_trace steps from
+    the seeded initial state (how a step's cost changes as the ink thread
+    grows)."""
+    import torch
+    shape = wl["shape"]
+    nsites = shape[0] * shape[1] * shape[2]
+    lat0.set_geometry(wl["geom"])
+    lat0.set_fields(rY, rB)
+    out = []
+    done = 0
+    while done < args.mlups_trace:
+        n = min(window, args.mlups_trace - done)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(lat0.stream)
+        lat0.step(n)
+        ev1.record(lat0.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / n
+        done += n
+        out.append({"steps": done, "ms_per_step": ms, "mlups": nsites / (ms * 1e-3) / 1e6})
+    out[-1]["unstable"] = lat0.diag()["unstable"]
+    lat0.set_geometry(wl["geom"])
+    lat0.set_fields(rY, rB)
+    return out
+
+
+def run_points(args, wl, rY, rB, device, lat0):
+    """MLUPS of the throughput lattice for power-law indices n = 0.4, 0.6, 0.8
+    (config 2's range; extrusion 0.02, head 0.01 l.u./step), each timed over
+    args.point_steps steps after the same spin-up as the headline."""
+    import torch
+    from paper_2102_02655_gb300 import lbm
+    shape = wl["shape"]
+    nsites = shape[0] * shape[1] * shape[2]
+    out = []
+    for n in (0.4, 0.6, 0.8):
+        lat0.set_geometry(wl["geom"])
+        lat0.set_rheology(dict(wl["rheo"], n=n))
+        lat0.set_fields(rY, rB)
+        lat0.step(args.spinup + args.warmup)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(lat0.stream)
+        lat0.step(args.point_steps)
+        ev1.record(lat0.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.point_steps
+        out.append({"n": n, "ms_per_step": ms, "mlups": nsites / (ms * 1e-3) / 1e6,
+                    "unstable": lat0.diag()["unstable"]})
+    lat0.set_geometry(wl["geom"])
+    lat0.set_rheology(wl["rheo"])
+    lat0.set_fields(rY, rB)
+    return out
 
 
 def sweep_workloads(n=64, seed=2024):
@@ -351,25 +426,30 @@ def run_sweep(args, device):
 
     sites = sum(w["shape"][0] * w["shape"][1] * w["shape"][2] for w in wls)
     K = args.sweep_steps
+    S = args.sweep_spinup
+    # autotuned plan; the batch also runs the untimed spin-up of both forms
+    # (the same state to rounding), so that both are timed past the fresh
+    # nozzle fill, where a step is cheaper
+    batch = lbm.Batch(lats)
+    tune = batch.autotune(trial_steps=4)
     # plain form: one lattice after another, each K steps on its own stream
     reset()
-    for lat in lats:
-        lat.step(1)
+    batch.step(1 + S)
+    batch.sync()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for lat in lats:
         lat.step(K)
         lat.stream.synchronize()
     t_plain = time.perf_counter() - t0
-    # batched form: autotuned plan, graphs captured, then K steps from the same state
-    batch = lbm.Batch(lats)
-    tune = batch.autotune(trial_steps=4)
+    # batched form: graphs of this call's sizes captured first, then K steps
+    # from the same spun-up state
     reset()
-    batch.step(1)
-    batch.step(K)  # captures the graphs of this call's sizes
+    batch.step(1 + S)
+    batch.step(K)
     batch.sync()
     reset()
-    batch.step(1)
+    batch.step(1 + S)
     batch.sync()
     t0 = time.perf_counter()
     batch.step(K)
@@ -391,8 +471,9 @@ def run_sweep(args, device):
                          "ms_per_step": tune["ms_per_step"], "candidates": len(tune["tried"])},
             "graph_steps": info["steps_per_graph"], "work_items": info["n_items"], "grid": info["grid"],
             "unstable": bad,
-            "what": "64 print runs 96^3..256x96x96 (seeded parameters), wall time of steps 2..K+1 from the "
-                    "seeded state for each form, host-synchronised"}
+            "spinup_steps": S,
+            "what": "64 print runs 96^3..256x96x96 (seeded parameters), wall time of K steps after the same "
+                    "untimed spin-up for each form, host-synchronised"}
 
 
 def serve_requests(n, steps_max, seed=5):
@@ -518,6 +599,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--spinup", type=int, default=2000,
+                    help="untimed steps before the warm-up (the ink thread forms)")
+    ap.add_argument("--point-steps", type=int, default=100, help="timed steps per ink-law point")
+    ap.add_argument("--no-points", action="store_true", help="skip the n = 0.4/0.6/0.8 points")
+    ap.add_argument("--mlups-trace", type=int, default=0,
+                    help="also time this many steps from the fresh state in windows of 500")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched parameter sweep")
@@ -530,6 +617,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--sweep-n", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=20)
+    ap.add_argument("--sweep-spinup", type=int, default=1000, help="untimed sweep steps before timing")
     ap.add_argument("--storage", choices=["f64", "f32", "f16dev", "bf16dev"], default=None,
                     help="population storage (default: the workload's, FP32)")
     ap.add_argument("--workload", default=WORKLOAD,

@@ -19,6 +19,9 @@
  *    the handle's device; others are host pointers. Field values are double
  *    for LBM_F64 storage and float otherwise (F32, F16DEV, BF16DEV).
  *  - Calls on one handle must not overlap (one host thread at a time).
+ *  - A call that touches the GPU makes the handle's device (cfg->device)
+ *    current while it runs and gives the caller's current device back on
+ *    return.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -143,7 +146,10 @@ lbm_status lbm_create(const lbm_config* cfg, struct lbm_handle** out);
 /* Set the print-head geometry and boundaries, reset the step counter and the
  * diagnostics, and initialise the state of Sec. III: the nozzle interior
  * above the gap filled with ink, ambient fluid elsewhere, all at rest, with
- * equilibrium populations. LBM_EINVAL for an inconsistent geometry. */
+ * equilibrium populations. LBM_EINVAL for an inconsistent geometry: non-finite
+ * values, |head_vel| or |u_ink| above 0.5, a gap outside [1, nz), and, with a
+ * nozzle, r_inner + wall_thickness above 2000 or nx, ny above 4000 (the
+ * fixed-point geometry of the nozzle squares distances in 64-bit integers). */
 lbm_status lbm_set_geometry(struct lbm_handle* h, const lbm_geometry* g);
 
 /* Set the ink rheology (Eq. 23-25). LBM_EINVAL if tau_min <= 1/2 or
@@ -232,8 +238,11 @@ lbm_status lbm_timings(struct lbm_handle* h, lbm_timing* out);
  *             created/destroyed mass; filling it waits for the stream.
  * The previous step's densities and top-plane velocities are rebuilt from
  * f_in (collision conserves each component's mass), so the result equals
- * lbm_step's up to rounding. The first call on a device looks up the static
- * array's device address; make that first call before any stream capture.
+ * lbm_step's up to rounding. Arguments pass the same checks as in lbm_create,
+ * lbm_set_geometry and lbm_set_ink_rheology. Each call looks up the static
+ * array's device address on cfg->device (no allocation); the first call on a
+ * device also loads the library's kernels there, so make that first call
+ * before any stream capture. The caller's current device is kept.
  * All calls share the one array and it keeps the last call's contents (the
  * call clears what must start at zero): calls that overlap on the GPU race,
  * so issue them on one stream or wait between them. Returns LBM_EINVAL for
@@ -283,8 +292,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Wait for the batch's stream. */
 lbm_status lbm_batch_sync(lbm_batch* b);
 
-/* Set the plan: variant 0 (32 x 8 tile columns) or 1 (32 x 16, FP32 storage
- * only) and, per lattice (host array of n ints), at most how many z-planes
+/* Set the plan: variant 0 (32 x 8 tile columns, the one bulk-kernel
+ * configuration; any other value is LBM_EINVAL) and, per lattice (host array of n ints), at most how many z-planes
  * one CTA of the bulk kernel marches up a column (the column's nz planes are
  * split into ceil(nz / zchunk) chunks whose lengths differ by at most one).
  * Waits for the batch's stream. */

@@ -33,14 +33,32 @@ def _nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(ROOT, "include", "lbm.h"))
+    files += [os.path.join(ROOT, "include", "lbm.h"), os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 
 
+def flag_set(extra=()):
+    """Every flag the library is compiled with, per translation unit."""
+    return "\n".join("%s: %s" % (src, " ".join(ARCH + FLAGS + FILE_FLAGS.get(src, []) + list(extra)))
+                     for src in SOURCES)
+
+
+def _stamp():
+    return os.path.join(OUT_DIR, "flags.txt")
+
+
 def build(force=False, verbose=False, extra=()):
-    """Compile (if sources changed) and return the library path."""
+    """Compile (if sources, this script or the flags changed) and return the
+    library path. The flags the library was built with are written beside it."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    flags = flag_set(extra)
+    fresh = os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps()
+    if fresh and os.path.exists(_stamp()):
+        with open(_stamp()) as f:
+            fresh = f.read() == flags
+    else:
+        fresh = False
+    if not force and fresh:
         return LIB
     nvcc = _nvcc()
 
@@ -62,6 +80,8 @@ def build(force=False, verbose=False, extra=()):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(_stamp(), "w") as f:
+        f.write(flags)
     return LIB
 
 

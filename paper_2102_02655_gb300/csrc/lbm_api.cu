@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <thread>
 #include <type_traits>
@@ -81,7 +80,6 @@ struct lbm_handle {
     long long step = 0; // steps since lbm_set_geometry
     long long launches = 0;
     int zchunk = 32;
-    int variant = 0;  // fused-kernel configuration (tuning knob CGLBM_FUSED_VARIANT)
     char err[256] = "";
     // event timing (lbm_profile)
     bool profiling = false;
@@ -150,6 +148,21 @@ void fill_model(const lbm_handle* h, StepArgs<real>& p) {
     p.beta = (real)c.beta;
     p.rho_ref = (real)c.rho0_amb;
     p.nuB = (real)((c.tau_ambient - 0.5) / 3.0);
+    {
+        // w_i rho_ref as the kernels round it, and the exact rounding offset of
+        // their sums that the FP32 ink-stress split needs (see moments())
+        double sw = 0.0, swx = 0.0;
+        const double R = (double)p.rho_ref;
+        for (int i = 0; i < h->Q; ++i) {
+            const double w = c.velset == LBM_D3Q19 ? D3Q19::w(i) : D2Q9::w(i);
+            const int cx = c.velset == LBM_D3Q19 ? D3Q19::c(i, 0) : D2Q9::c(i, 0);
+            p.wref[i] = (real)(w * R);
+            sw += (double)p.wref[i];
+            swx += (double)p.wref[i] * cx * cx;
+        }
+        for (int i = h->Q; i < kMaxQ; ++i) p.wref[i] = 0;
+        p.kappa_w = (real)((swx - R / 3.0) - (sw - R) / 3.0);
+    }
     for (int a = 0; a < 3; ++a) p.g[a] = (real)c.body_force[a];
     p.drag_gamma = (real)c.drag_gamma;
     p.drag_height = (real)c.drag_height;
@@ -355,7 +368,7 @@ lbm_status do_steps(lbm_handle* h, int nsteps) {
                 if ((st = mark(h, 1, true, box_sites, h->side)) != LBM_OK) return st;
             }
             if ((st = mark(h, 0, false, 0, h->stream)) != LBM_OK) return st;
-            launched += launch_fused<real, S>(p, h->zchunk, h->stream, h->variant);
+            launched += launch_fused<real, S>(p, h->zchunk, h->stream);
             if ((st = mark(h, 0, true, h->N - box_sites, h->stream)) != LBM_OK) return st;
             if (box.wx > 0) {
                 cudaError_t e = cudaEventRecord(h->join, h->side);
@@ -408,15 +421,111 @@ lbm_status dispatch_init(lbm_handle* h, int staged, int have_u) {
     }
 }
 
-lbm_status check_usable(lbm_handle* h) {
-    if (!h) return LBM_EINVAL;
+// Makes a handle's device current for the duration of an API call and gives
+// the caller's current device back on return.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) err = cudaSetDevice(dev);
+        else prev = -1;  // nothing to give back
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
+lbm_status check_usable(lbm_handle* h, const DeviceScope& ds) {
     if (h->dead) return fail(h, LBM_ECUDA, "handle unusable after an earlier CUDA error");
-    cudaError_t e = cudaSetDevice(h->cfg.device);
-    if (e != cudaSuccess) return cuda_check(h, e, "cudaSetDevice");
+    if (ds.err != cudaSuccess) return cuda_check(h, ds.err, "cudaSetDevice");
     return LBM_OK;
 }
 
 bool finite_d(double v) { return std::isfinite(v); }
+bool all_finite(const double* v, int n) {
+    for (int k = 0; k < n; ++k)
+        if (!finite_d(v[k])) return false;
+    return true;
+}
+
+// Largest lattice side (x, y) and nozzle radius r_inner + wall_thickness
+// (lattice units) of a run with a nozzle: the fixed-point geometry squares
+// distances of up to half a side, and the radii, in units of 2^-20 in 64-bit
+// integers, which stays exact below these bounds (2 (2000 * 2^20)^2 < 2^63).
+constexpr int kMaxNozzleSide = 4000;
+constexpr double kMaxNozzleRadius = 2000.0;
+
+// The checks every entry point applies to a configuration, a geometry and a
+// rheology. Each returns nullptr when the argument is valid, else what is
+// wrong with it.
+const char* config_problem(const lbm_config* c) {
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return "lattice sizes must be >= 1";
+    if (c->velset != LBM_D2Q9 && c->velset != LBM_D3Q19) return "unknown velocity set";
+    if (c->velset == LBM_D2Q9 && c->ny != 1) return "D2Q9 lattices lie in the x-z plane, ny must be 1";
+    if (c->storage < LBM_F64 || c->storage > LBM_BF16DEV) return "unknown storage";
+    if (c->path < LBM_PATH_AUTO || c->path > LBM_PATH_FUSED) return "unknown path";
+    if (c->path == LBM_PATH_FUSED && c->velset != LBM_D3Q19) return "the fused path needs D3Q19";
+    if ((double)c->nx * c->ny * c->nz > 4.0e9) return "lattice too large";
+    if (!(c->tau_ambient > 0.5) || !finite_d(c->tau_ambient)) return "tau_ambient must be > 1/2 and finite";
+    if (!(c->rho0_ink > 0) || !(c->rho0_amb > 0) || !finite_d(c->rho0_ink) || !finite_d(c->rho0_amb))
+        return "reference densities must be > 0 and finite";
+    if (!(c->alpha_ink < 1.0) || !(c->alpha_amb < 1.0)) return "alpha must be < 1";
+    if (!(c->beta >= 0.0 && c->beta <= 1.0)) return "beta must be in [0, 1]";
+    if (!finite_d(c->A) || !(c->zeta_ink > 0) || !(c->zeta_amb > 0) || !finite_d(c->zeta_ink) ||
+        !finite_d(c->zeta_amb) || !finite_d(c->drag_gamma) || !finite_d(c->drag_height) ||
+        !all_finite(c->body_force, 3))
+        return "invalid A, zeta, drag or body force";
+    if ((c->alloc == nullptr) != (c->free == nullptr)) return "alloc and free must be given together";
+    return nullptr;
+}
+
+const char* geometry_problem(const lbm_config* c, const lbm_geometry* g) {
+    if (g->z_mode != LBM_Z_PERIODIC && g->z_mode != LBM_Z_WALLS) return "unknown z_mode";
+    if (g->top_mode != LBM_TOP_OPEN && g->top_mode != LBM_TOP_WALL) return "unknown top_mode";
+    for (int a = 0; a < 2; ++a)
+        if (!finite_d(g->head_pos[a]) || !finite_d(g->head_vel[a]) || std::fabs(g->head_vel[a]) > 0.5)
+            return "head position/velocity invalid (finite, |v| <= 0.5)";
+    if (!all_finite(g->top_vel, 3)) return "top_vel must be finite";
+    if (g->nozzle) {
+        if (g->z_mode != LBM_Z_WALLS) return "the nozzle needs z walls";
+        if (g->gap < 1 || g->gap >= c->nz) return "gap must be in [1, nz)";
+        if (!(g->r_inner > 0) || !(g->wall_thickness > 0) || !(g->r_inner + g->wall_thickness <= kMaxNozzleRadius))
+            return "radii must be positive with r_inner + wall_thickness <= 2000";
+        if (c->nx > kMaxNozzleSide || c->ny > kMaxNozzleSide) return "a nozzle run needs nx, ny <= 4000";
+        if (!finite_d(g->u_ink) || std::fabs(g->u_ink) > 0.5) return "|u_ink| must be <= 0.5";
+    }
+    if (g->z_mode == LBM_Z_WALLS && g->top_mode == LBM_TOP_OPEN && !(g->rho_top_amb > 0 && finite_d(g->rho_top_amb)))
+        return "rho_top_amb must be > 0 and finite";
+    return nullptr;
+}
+
+const char* rheology_problem(const lbm_rheology* r) {
+    if (!(r->tau_min > 0.5) || !(r->tau_max >= r->tau_min) || !finite_d(r->tau_max))
+        return "need 1/2 < tau_min <= tau_max, finite";
+    if (!finite_d(r->tol) || r->tol < 0 || r->max_iter < 0) return "tol and max_iter must be >= 0";
+    switch (r->law) {
+    case LBM_NEWTONIAN:
+        if (!(r->nu0 > 0) || !finite_d(r->nu0)) return "nu0 must be > 0 and finite";
+        return nullptr;
+    case LBM_CROSS:
+        if (!(r->nu0 > 0) || !(r->nu_inf >= 0) || !(r->lambda > 0) || !(r->n > 0) || !finite_d(r->nu0) ||
+            !finite_d(r->nu_inf) || !finite_d(r->lambda) || !finite_d(r->n))
+            return "Cross needs finite nu0 > 0, nu_inf >= 0, lambda > 0, n > 0";
+        return nullptr;
+    case LBM_POWER_LAW:
+        if (!(r->K > 0) || !(r->n > 0) || !finite_d(r->K) || !finite_d(r->n))
+            return "power law needs finite K > 0, n > 0";
+        return nullptr;
+    default:
+        return "unknown law";
+    }
+}
 
 }  // namespace
 
@@ -426,32 +535,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     if (!out) return fail(nullptr, LBM_EINVAL, "lbm_create: out is NULL");
     *out = nullptr;
     if (!cfg) return fail(nullptr, LBM_EINVAL, "lbm_create: cfg is NULL");
-    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: lattice sizes must be >= 1");
-    if (cfg->velset != LBM_D2Q9 && cfg->velset != LBM_D3Q19)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: unknown velocity set %d", cfg->velset);
-    if (cfg->velset == LBM_D2Q9 && cfg->ny != 1)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: D2Q9 lattices lie in the x-z plane, ny must be 1");
-    if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16DEV)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: unknown storage %d", cfg->storage);
-    if (cfg->path < LBM_PATH_AUTO || cfg->path > LBM_PATH_FUSED)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: unknown path %d", cfg->path);
-    if (cfg->path == LBM_PATH_FUSED && cfg->velset != LBM_D3Q19)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: the fused path needs D3Q19");
-    const double N = (double)cfg->nx * cfg->ny * cfg->nz;
-    if (N > 4.0e9) return fail(nullptr, LBM_EINVAL, "lbm_create: lattice too large");
-    if (!(cfg->tau_ambient > 0.5) || !finite_d(cfg->tau_ambient))
-        return fail(nullptr, LBM_EINVAL, "lbm_create: tau_ambient must be > 1/2");
-    if (!(cfg->rho0_ink > 0) || !(cfg->rho0_amb > 0))
-        return fail(nullptr, LBM_EINVAL, "lbm_create: reference densities must be > 0");
-    if (cfg->alpha_ink >= 1.0 || cfg->alpha_amb >= 1.0)
-        return fail(nullptr, LBM_EINVAL, "lbm_create: alpha must be < 1");
-    if (!(cfg->beta >= 0.0 && cfg->beta <= 1.0))
-        return fail(nullptr, LBM_EINVAL, "lbm_create: beta must be in [0, 1]");
-    if (!finite_d(cfg->A) || !(cfg->zeta_ink > 0) || !(cfg->zeta_amb > 0) || !finite_d(cfg->drag_gamma))
-        return fail(nullptr, LBM_EINVAL, "lbm_create: invalid A, zeta or drag");
-    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
-        return fail(nullptr, LBM_EINVAL, "lbm_create: alloc and free must be given together");
+    if (const char* m = config_problem(cfg)) return fail(nullptr, LBM_EINVAL, "lbm_create: %s", m);
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return fail(nullptr, LBM_ENOMEM, "lbm_create: host allocation failed");
@@ -471,10 +555,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));
         h->zchunk = std::max(4, (int)((cfg->nz + chunks - 1) / chunks));
         if (const char* e = getenv("CGLBM_ZCHUNK")) h->zchunk = std::max(1, atoi(e));
-        if (const char* e = getenv("CGLBM_FUSED_VARIANT")) h->variant = atoi(e);
     }
 
-    cudaError_t e = cudaSetDevice(cfg->device);
+    DeviceScope ds(cfg->device);
+    cudaError_t e = ds.err;
     if (e != cudaSuccess) {
         fail(nullptr, LBM_ECUDA, "lbm_create: cudaSetDevice(%d): %s", cfg->device, cudaGetErrorString(e));
         delete h;
@@ -534,27 +618,12 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
 }
 
 lbm_status lbm_set_geometry(lbm_handle* h, const lbm_geometry* g) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!g) return fail(h, LBM_EINVAL, "lbm_set_geometry: g is NULL");
-    if (g->z_mode != LBM_Z_PERIODIC && g->z_mode != LBM_Z_WALLS)
-        return fail(h, LBM_EINVAL, "lbm_set_geometry: unknown z_mode");
-    if (g->top_mode != LBM_TOP_OPEN && g->top_mode != LBM_TOP_WALL)
-        return fail(h, LBM_EINVAL, "lbm_set_geometry: unknown top_mode");
-    for (int a = 0; a < 2; ++a)
-        if (!finite_d(g->head_pos[a]) || !finite_d(g->head_vel[a]) || std::fabs(g->head_vel[a]) > 0.5)
-            return fail(h, LBM_EINVAL, "lbm_set_geometry: head position/velocity invalid (|v| <= 0.5)");
-    if (g->nozzle) {
-        if (g->z_mode != LBM_Z_WALLS) return fail(h, LBM_EINVAL, "lbm_set_geometry: the nozzle needs z walls");
-        if (g->gap < 1 || g->gap >= h->cfg.nz)
-            return fail(h, LBM_EINVAL, "lbm_set_geometry: gap must be in [1, nz)");
-        if (!(g->r_inner > 0) || !(g->wall_thickness > 0) || g->r_inner + g->wall_thickness > 1e5)
-            return fail(h, LBM_EINVAL, "lbm_set_geometry: radii must be positive");
-        if (!finite_d(g->u_ink) || std::fabs(g->u_ink) > 0.5)
-            return fail(h, LBM_EINVAL, "lbm_set_geometry: |u_ink| must be <= 0.5");
-    }
-    if (!(g->rho_top_amb > 0) && g->z_mode == LBM_Z_WALLS && g->top_mode == LBM_TOP_OPEN)
-        return fail(h, LBM_EINVAL, "lbm_set_geometry: rho_top_amb must be > 0");
+    if (const char* m = geometry_problem(&h->cfg, g)) return fail(h, LBM_EINVAL, "lbm_set_geometry: %s", m);
     h->geom = *g;
     h->have_geom = true;
     h->step = 0;
@@ -562,33 +631,21 @@ lbm_status lbm_set_geometry(lbm_handle* h, const lbm_geometry* g) {
 }
 
 lbm_status lbm_set_ink_rheology(lbm_handle* h, const lbm_rheology* r) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!r) return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: r is NULL");
-    if (!(r->tau_min > 0.5) || !(r->tau_max >= r->tau_min) || !finite_d(r->tau_max))
-        return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: need 1/2 < tau_min <= tau_max");
-    switch (r->law) {
-    case LBM_NEWTONIAN:
-        if (!(r->nu0 > 0)) return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: nu0 must be > 0");
-        break;
-    case LBM_CROSS:
-        if (!(r->nu0 > 0) || !(r->nu_inf >= 0) || !(r->lambda > 0) || !(r->n > 0))
-            return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: Cross needs nu0 > 0, nu_inf >= 0, lambda > 0, n > 0");
-        break;
-    case LBM_POWER_LAW:
-        if (!(r->K > 0) || !(r->n > 0))
-            return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: power law needs K > 0, n > 0");
-        break;
-    default:
-        return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: unknown law %d", r->law);
-    }
+    if (const char* m = rheology_problem(r)) return fail(h, LBM_EINVAL, "lbm_set_ink_rheology: %s", m);
     h->rheo = *r;
     h->have_rheo = true;
     return LBM_OK;
 }
 
 lbm_status lbm_set_fields(lbm_handle* h, const void* rho_ink, const void* rho_amb, const void* u, int on_device) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!h->have_geom) return fail(h, LBM_ESTATE, "lbm_set_fields: set the geometry first");
     if (!rho_ink || !rho_amb) return fail(h, LBM_EINVAL, "lbm_set_fields: densities are NULL");
@@ -603,7 +660,9 @@ lbm_status lbm_set_fields(lbm_handle* h, const void* rho_ink, const void* rho_am
 }
 
 lbm_status lbm_step(lbm_handle* h, int nsteps) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!h->have_geom || !h->have_rheo) return fail(h, LBM_ESTATE, "lbm_step: geometry and rheology must be set");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "lbm_step: nsteps < 0");
@@ -619,7 +678,9 @@ lbm_status lbm_step(lbm_handle* h, int nsteps) {
 }
 
 lbm_status lbm_sync(lbm_handle* h, int timeout_ms) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (timeout_ms <= 0) return cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     const auto t0 = std::chrono::steady_clock::now();
@@ -635,7 +696,9 @@ lbm_status lbm_sync(lbm_handle* h, int timeout_ms) {
 }
 
 lbm_status lbm_fields(lbm_handle* h, unsigned mask, void* const* dst, int dst_on_device, lbm_diag* diag) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!h->have_geom) return fail(h, LBM_ESTATE, "lbm_fields: no state yet");
     if (mask & ~0x7Fu) return fail(h, LBM_EINVAL, "lbm_fields: unknown bits in mask");
@@ -683,7 +746,7 @@ lbm_status lbm_fields(lbm_handle* h, unsigned mask, void* const* dst, int dst_on
 
 void lbm_destroy(lbm_handle* h) {
     if (!h) return;
-    cudaSetDevice(h->cfg.device);
+    DeviceScope ds(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (int b = 0; b < 2; ++b) {
         dev_free(h, h->f[b]);
@@ -713,7 +776,9 @@ const char* lbm_last_error(const lbm_handle* h) { return h ? h->err : g_create_e
 long long lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
 
 lbm_status lbm_profile(lbm_handle* h, int enable) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (enable) {
         h->nev[0] = h->nev[1] = 0;
@@ -724,7 +789,9 @@ lbm_status lbm_profile(lbm_handle* h, int enable) {
 }
 
 lbm_status lbm_timings(lbm_handle* h, lbm_timing* out) {
-    lbm_status st = check_usable(h);
+    if (!h) return LBM_EINVAL;
+    DeviceScope ds(h->cfg.device);
+    lbm_status st = check_usable(h, ds);
     if (st != LBM_OK) return st;
     if (!out) return fail(h, LBM_EINVAL, "lbm_timings: out is NULL");
     st = fold_events(h);
@@ -743,23 +810,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCR
 
 namespace {
 
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
-
 // In host code g_noalloc_scratch names a host-side stand-in, not device
-// memory: the kernels get the address that the runtime reports for the
-// current device, looked up once per device.
-lbm_status noalloc_scratch(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= 64) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: device %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = ptr;
-    }
-    *out = (unsigned char*)g_noalloc_addr[dev];
+// memory: the kernels get the address the runtime reports for the current
+// device, looked up on every call (no allocation; a device reset between
+// calls cannot leave a stale address behind).
+lbm_status noalloc_scratch(unsigned char** out) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+        return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    *out = (unsigned char*)ptr;
     return LBM_OK;
 }
 
@@ -827,18 +887,16 @@ lbm_status noalloc_step(lbm_handle* tmp, long long step, const void* f_in, void*
 extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry* g, const lbm_rheology* r,
                                        long long step, const void* f_in, void* f_out, void* fields, lbm_diag* diag) {
     if (!cfg || !g || !r) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: cfg, g and r are required");
-    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || (cfg->velset != LBM_D2Q9 && cfg->velset != LBM_D3Q19) ||
-        (cfg->velset == LBM_D2Q9 && cfg->ny != 1) || (cfg->storage != LBM_F64 && cfg->storage != LBM_F32))
-        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid lattice sizes, velocity set or storage");
-    if (!(cfg->tau_ambient > 0.5) || !(cfg->rho0_ink > 0) || !(cfg->rho0_amb > 0) || cfg->alpha_ink >= 1.0 ||
-        cfg->alpha_amb >= 1.0 || !(cfg->beta >= 0.0 && cfg->beta <= 1.0))
-        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid model constants");
-    if (!(r->tau_min > 0.5) || !(r->tau_max >= r->tau_min) || r->law < LBM_NEWTONIAN || r->law > LBM_POWER_LAW)
-        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid rheology");
-    if ((g->z_mode != LBM_Z_PERIODIC && g->z_mode != LBM_Z_WALLS) || (g->top_mode != LBM_TOP_OPEN && g->top_mode != LBM_TOP_WALL) ||
-        (g->nozzle && (g->z_mode != LBM_Z_WALLS || g->gap < 1 || g->gap >= cfg->nz || !(g->r_inner > 0) ||
-                       !(g->wall_thickness > 0))))
-        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: invalid geometry");
+    // the same checks as lbm_create, lbm_set_geometry and lbm_set_ink_rheology
+    lbm_config c = *cfg;
+    c.path = LBM_PATH_PLAIN;
+    c.alloc = nullptr;
+    c.free = nullptr;
+    if (const char* m = config_problem(&c)) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: %s", m);
+    if (cfg->storage != LBM_F64 && cfg->storage != LBM_F32)
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: storage must be LBM_F64 or LBM_F32");
+    if (const char* m = geometry_problem(cfg, g)) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: %s", m);
+    if (const char* m = rheology_problem(r)) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: %s", m);
     if (step < 1) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: step must be >= 1");
     if (!f_in || !f_out) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: f_in and f_out are required");
     const int Q = cfg->velset == LBM_D3Q19 ? 19 : 9;
@@ -854,10 +912,11 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const lbm_geometry
         return fail(nullptr, LBM_EINVAL,
                     "lbm_step_noalloc: the lattice needs %zu bytes of work space, the static array holds %u", need,
                     (unsigned)LBM_NOALLOC_SCRATCH_BYTES);
-    cudaError_t e = cudaSetDevice(cfg->device);
-    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaSetDevice: %s", cudaGetErrorString(e));
+    DeviceScope ds(cfg->device);
+    if (ds.err != cudaSuccess)
+        return fail(nullptr, LBM_ECUDA, "lbm_step_noalloc: cudaSetDevice: %s", cudaGetErrorString(ds.err));
     unsigned char* scratch = nullptr;
-    lbm_status st = noalloc_scratch(cfg->device, &scratch);
+    lbm_status st = noalloc_scratch(&scratch);
     if (st != LBM_OK) return st;
     // the constants come from the same host code as lbm_step's, through a
     // handle object on the stack that owns no device memory
@@ -962,8 +1021,7 @@ long long plan_items(const int* dims, int n, int tile_h, const int* zchunk, int*
 template <typename real, typename S>
 lbm_status batch_plan(lbm_batch* b, int variant, const std::vector<int>& zc) {
     const int L = (int)b->lat.size();
-    const bool fp64 = sizeof(real) == 8;
-    const int th = fused_tile_height(variant, fp64);
+    const int th = kFusedTileH;
     std::vector<int> dims(3 * L);
     for (int l = 0; l < L; ++l) {
         dims[3 * l] = b->lat[l]->cfg.nx;
@@ -990,7 +1048,7 @@ lbm_status batch_plan(lbm_batch* b, int variant, const std::vector<int>& zc) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lbm_batch: work list upload");
     int occ = 0, sms = 0;
-    launch_fused_batch<real, S>(nullptr, nullptr, 0, nullptr, 0, b->unit, variant, b->stream, &occ);
+    launch_fused_batch<real, S>(nullptr, nullptr, 0, nullptr, 0, b->unit, b->stream, &occ);
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return bcuda(b, e, "cudaDeviceGetAttribute");
     b->n_items = (int)n;
@@ -1033,7 +1091,7 @@ lbm_status batch_capture(lbm_batch* b, int slot, int g) {
         e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
         if (e != cudaSuccess) break;
         launch_fused_batch<real, S>(args + (size_t)k * L, b->d_items, b->n_items, b->d_queue + k, b->grid, b->unit,
-                                    b->variant, b->stream, nullptr);
+                                    b->stream, nullptr);
         e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
     }
@@ -1176,11 +1234,9 @@ struct RunAlloc {
     static lbm_status run(lbm_batch* b) { return batch_alloc_tables<real, S>(b); }
 };
 
-lbm_status batch_usable(lbm_batch* b) {
-    if (!b) return LBM_EINVAL;
+lbm_status batch_usable(lbm_batch* b, const DeviceScope& ds) {
     if (b->dead) return bfail(b, LBM_ECUDA, "batch unusable after an earlier CUDA error");
-    cudaError_t e = cudaSetDevice(b->device);
-    if (e != cudaSuccess) return bcuda(b, e, "cudaSetDevice");
+    if (ds.err != cudaSuccess) return bcuda(b, ds.err, "cudaSetDevice");
     for (lbm_handle* h : b->lat)
         if (h->dead) return bfail(b, LBM_ECUDA, "a lattice of the batch is unusable after a CUDA error");
     return LBM_OK;
@@ -1292,7 +1348,8 @@ lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out)
     if (!b) return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: host allocation failed");
     b->device = lattices[0]->cfg.device;
     b->storage = lattices[0]->cfg.storage;
-    cudaError_t e = cudaSetDevice(b->device);
+    DeviceScope ds(b->device);
+    cudaError_t e = ds.err;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = create_box_stream(&b->side);
     for (cudaEvent_t* ev : {&b->fork, &b->join, &b->done, &b->h_ev[0], &b->h_ev[1]})
@@ -1315,7 +1372,9 @@ lbm_status lbm_batch_create(lbm_handle* const* lattices, int n, lbm_batch** out)
 }
 
 lbm_status lbm_batch_reset(lbm_batch* b, lbm_handle* const* lattices, int n) {
-    lbm_status st = batch_usable(b);
+    if (!b) return LBM_EINVAL;
+    DeviceScope ds(b->device);
+    lbm_status st = batch_usable(b, ds);
     if (st != LBM_OK) return st;
     int unit = 1;
     if ((st = batch_check(b, lattices, n, &unit)) != LBM_OK) return st;
@@ -1326,7 +1385,9 @@ lbm_status lbm_batch_reset(lbm_batch* b, lbm_handle* const* lattices, int n) {
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
-    lbm_status st = batch_usable(b);
+    if (!b) return LBM_EINVAL;
+    DeviceScope ds(b->device);
+    lbm_status st = batch_usable(b, ds);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: nsteps < 0");
     if (nsteps == 0) return LBM_OK;
@@ -1334,11 +1395,11 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
 }
 
 lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk) {
-    lbm_status st = batch_usable(b);
+    if (!b) return LBM_EINVAL;
+    DeviceScope ds(b->device);
+    lbm_status st = batch_usable(b, ds);
     if (st != LBM_OK) return st;
-    if (variant < 0 || variant > 1) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: variant must be 0 or 1");
-    if (variant == 1 && b->storage != LBM_F32)
-        return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: 32 x 16 tiles (variant 1) need FP32 storage");
+    if (variant != 0) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: variant must be 0");
     if (!zchunk) return bfail(b, LBM_EINVAL, "lbm_batch_set_plan: zchunk is NULL");
     std::vector<int> zc(zchunk, zchunk + b->lat.size());
     for (int v : zc)
@@ -1349,14 +1410,16 @@ lbm_status lbm_batch_set_plan(lbm_batch* b, int variant, const int* zchunk) {
 }
 
 lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_tuning* out) {
-    lbm_status st = batch_usable(b);
+    if (!b) return LBM_EINVAL;
+    DeviceScope ds(b->device);
+    lbm_status st = batch_usable(b, ds);
     if (st != LBM_OK) return st;
     if (trial_steps < 1) return bfail(b, LBM_EINVAL, "lbm_batch_autotune: trial_steps < 1");
     const int L = (int)b->lat.size();
     int max_nz = 1;
     for (lbm_handle* h : b->lat) max_nz = std::max(max_nz, h->cfg.nz);
     const int chunks[] = {8, 12, 16, 24, 32, 48, 64, 96, 128};
-    const int nvar = b->storage == LBM_F32 ? 2 : 1;  // 32 x 16 tiles: FP32 storage only
+    const int nvar = 1;  // one bulk-kernel configuration
     lbm_batch_tuning res;
     memset(&res, 0, sizeof(res));
     res.ms_per_step = 1e30;
@@ -1419,7 +1482,7 @@ lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_plan_info* out) {
     if (!b || !out) return LBM_EINVAL;
     out->n_lattices = (int)b->lat.size();
     out->variant = b->variant;
-    out->tile_h = fused_tile_height(b->variant, b->storage == LBM_F64);
+    out->tile_h = kFusedTileH;
     out->n_items = b->n_items;
     out->grid = b->grid;
     out->steps_per_graph = b->G;
@@ -1429,14 +1492,16 @@ lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_plan_info* out) {
 }
 
 lbm_status lbm_batch_sync(lbm_batch* b) {
-    lbm_status st = batch_usable(b);
+    if (!b) return LBM_EINVAL;
+    DeviceScope ds(b->device);
+    lbm_status st = batch_usable(b, ds);
     if (st != LBM_OK) return st;
     return bcuda(b, cudaStreamSynchronize(b->stream), "lbm_batch_sync");
 }
 
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
-    cudaSetDevice(b->device);
+    DeviceScope ds(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->side) cudaStreamSynchronize(b->side);
     for (cudaGraphExec_t x : b->exec)

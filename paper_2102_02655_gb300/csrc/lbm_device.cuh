@@ -138,6 +138,8 @@ struct __align__(16) StepArgs {
     real dphi[2][kMaxQ];  // phi^k_i - w_i (zero at density ratio one)
     real pfac[2];      // p^k = pfac[k] rho^k (Eq. 9)
     real rho_ref;      // reference total density of the stored deviation
+    real wref[kMaxQ];  // w_i rho_ref, rounded to the compute type
+    real kappa_w;      // sum_i wref_i c_ix^2 - rho_ref/3 - (sum_i wref_i - rho_ref)/3, exact
     int unit;          // rho0_ink == rho0_amb and phi = w for both (density ratio one)
     int law, max_iter;
     real nu0, nu_inf, lambda, n_exp, K, tau_min, tau_max, tol;
@@ -530,6 +532,17 @@ __device__ __forceinline__ double qsqrt<double>(double a) { return sqrt(a); }
 template <>
 __device__ __forceinline__ float qsqrt<float>(float a) { return a > 0.0f ? a * rsqrtf(a) : 0.0f; }
 
+// Square of the |grad rho^N| at or below which the recolouring direction of
+// Eq. 16 is undefined: 2^8 units of rounding of the arithmetic, 2^-45 in FP64
+// and 2^-16 in FP32 (the colour fractions the gradient is formed from carry a
+// few units of rounding each).
+template <typename real>
+__device__ __forceinline__ constexpr real grad_floor2();
+template <>
+__device__ __forceinline__ constexpr double grad_floor2<double>() { return 0x1p-90; }
+template <>
+__device__ __forceinline__ constexpr float grad_floor2<float>() { return 0x1p-32f; }
+
 // ink fraction rho_Y / (rho_Y + rho_B) of a site's densities
 template <typename real>
 __device__ __forceinline__ real colour_frac(real a, real b) { return qdiv(a, a + b); }
@@ -638,54 +651,33 @@ struct Moments {
     real PT[6];    // mixture non-equilibrium stress
 };
 
-// FP32 storage: where the ink carries the rheology (rho_Y > 1e-3 rho), its
-// stress is summed in double (the populations convert exactly, and so does
-// the sum of two), so that only the storage rounding of f^Y remains, not the
-// cancellation in the sums. u is the FP32 velocity of the site.
+// Moments of a site after streaming (Eq. 2-3, 20).
+//
+// The ink's non-equilibrium stress Pi^Y = sum_i f^Y_i c_i c_i - rho_Y (p_Y I
+// + u u) is a difference of O(rho_Y) numbers that is 10^-3..10^-4 of them in
+// the print flow, and the shear rate of Eq. 24 is read from it. In FP64 it is
+// summed as written. In FP32 the direct sum would lose about 3 digits to that
+// cancellation, so the stress is taken apart exactly: with c = rho_Y / rho
+// and the ink's excess over its share of the total, h_i = f^Y_i - c f_i
+// (f_i = W_i + d_i, W_i = w_i rho_ref as rounded in p.wref),
+//   sum_i f^Y_i c_i c_i = c (sum_i W_i c_i c_i + sum_i d_i c_i c_i) + sum_i h_i c_i c_i,
+// which for any c gives
+//   Pi^Y = c Pi + H - (sum_i h_i)(I/3 + u u) + c kappa I   (density ratio one),
+// Pi the mixture stress (formed from the small deviations d_i), H the second
+// moment of h and kappa the rounding of the weights, sum_i W_i c_x^2 - rho_ref/3
+// - (sum_i W_i - rho_ref)/3 (p.kappa_w, exact on the host). h_i is small
+// (the recolouring term and the rounding of the stored values), so the sums
+// carry no cancellation and every operation stays in FP32.
+template <typename T>
+__device__ __forceinline__ T rfma(T a, T b, T c) { return fma(a, b, c); }
+
 template <class VS, typename real>
-__device__ __forceinline__ void ink_stress_exact(const StepArgs<real>& p, const real fy[VS::Q], real ux, real uy,
-                                                 real uz, real PY[6]) {
-    constexpr int Q = VS::Q;
-    double c[6] = {0, 0, 0, 0, 0, 0};
-    double rYd = (double)fy[0];
-#pragma unroll
-    for (int q = 0; q < (Q - 1) / 2; ++q) {
-        const int i = 2 * q + 1;
-        const double v = (double)fy[i] + (double)fy[i + 1];
-        const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-        rYd += v;
-        if (cx) c[0] += v;
-        if (cy) c[1] += v;
-        if (cz) c[2] += v;
-        if (cx && cy) c[3] += (cx == cy) ? v : -v;
-        if (cx && cz) c[4] += (cx == cz) ? v : -v;
-        if (cy && cz) c[5] += (cy == cz) ? v : -v;
-    }
-    const double uxd = ux, uyd = uy, uzd = uz, pYd = (double)p.pfac[0] * rYd;
-    PY[0] = (real)(c[0] - (pYd + rYd * uxd * uxd));
-    PY[1] = (real)(c[1] - (pYd + rYd * uyd * uyd));
-    PY[2] = (real)(c[2] - (pYd + rYd * uzd * uzd));
-    PY[3] = (real)(c[3] - rYd * uxd * uyd);
-    PY[4] = (real)(c[4] - rYd * uxd * uzd);
-    PY[5] = (real)(c[5] - rYd * uyd * uzd);
-    if (VS::kPlanar) PY[1] = PY[3] = PY[5] = 0;
-}
-
-// the sites where ink_stress_exact applies
-template <typename real>
-__device__ __forceinline__ bool ink_exact_site(real rY, real rho) {
-    return sizeof(real) < sizeof(double) && rY > real(1e-3) * rho;
-}
-
-// kExact = false leaves PY in FP32 everywhere: the caller applies
-// ink_stress_exact where ink_exact_site holds (the fused kernel, which stages
-// the moments, does so at the collision)
-template <class VS, typename real, bool kExact = true>
 __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2][VS::Q], Moments<real>* M) {
     constexpr int Q = VS::Q;
-    // moments (Eq. 2-3) and the second moments of the ink and of the total
-    // deviation, accumulated direction by direction (17 running sums): ink
-    // density from slot 0, total density and momentum from the deviation slot
+    constexpr bool kSplit = sizeof(real) < sizeof(double);
+    // moments (Eq. 2-3) and the second moments of the total deviation (and,
+    // in FP64, of the ink), accumulated direction by direction: ink density
+    // from slot 0, total density and momentum from the deviation slot
     // (sum_i w_i c_i = 0). The densities are summed in direction order, as
     // every density of the step is, so that a site's colour fraction is the
     // same bit for bit wherever it is computed.
@@ -700,24 +692,32 @@ __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2]
         if (cx) mx += cx > 0 ? fd : -fd;
         if (cy) my += cy > 0 ? fd : -fd;
         if (cz) mz += cz > 0 ? fd : -fd;
-        if (cx) { a[0] += fy; b[0] += fd; }
-        if (cy) { a[1] += fy; b[1] += fd; }
-        if (cz) { a[2] += fy; b[2] += fd; }
-        if (cx && cy) { a[3] += (cx == cy) ? fy : -fy; b[3] += (cx == cy) ? fd : -fd; }
-        if (cx && cz) { a[4] += (cx == cz) ? fy : -fy; b[4] += (cx == cz) ? fd : -fd; }
-        if (cy && cz) { a[5] += (cy == cz) ? fy : -fy; b[5] += (cy == cz) ? fd : -fd; }
+        if (cx) b[0] += fd;
+        if (cy) b[1] += fd;
+        if (cz) b[2] += fd;
+        if (cx && cy) b[3] += (cx == cy) ? fd : -fd;
+        if (cx && cz) b[4] += (cx == cz) ? fd : -fd;
+        if (cy && cz) b[5] += (cy == cz) ? fd : -fd;
+        if constexpr (!kSplit) {
+            if (cx) a[0] += fy;
+            if (cy) a[1] += fy;
+            if (cz) a[2] += fy;
+            if (cx && cy) a[3] += (cx == cy) ? fy : -fy;
+            if (cx && cz) a[4] += (cx == cz) ? fy : -fy;
+            if (cy && cz) a[5] += (cy == cz) ? fy : -fy;
+        }
     }
     const real rho = p.rho_ref + sd;
     const real rB = rho - rY;
     const real irho = qdiv(real(1), rho);
     const real ux = mx * irho, uy = my * irho, uz = mz * irho;
 
-    // non-equilibrium stresses (Eq. 20): ink Pi^Y = sum f^Y c c - rY (pfac_Y I + u u),
-    // mixture Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
+    // mixture non-equilibrium stress (Eq. 20):
+    // Pi = sum d c c - [sum_k rho_k pfac_k - rho_ref c_s^2] I - rho u u
     real* PY = M->PY;
     real* PT = M->PT;
-    const real pY = p.pfac[0] * rY;
-    real pT = (rho - p.rho_ref) * real(1.0 / 3.0);
+    // (rho - rho_ref) c_s^2 formed from sd itself, not from the rounded rho
+    real pT = sd * real(1.0 / 3.0);
     if (!p.unit) pT += rY * (p.pfac[0] - real(1.0 / 3.0)) + rB * (p.pfac[1] - real(1.0 / 3.0));
     PT[0] = b[0] - (pT + rho * ux * ux);
     PT[1] = b[1] - (pT + rho * uy * uy);
@@ -725,13 +725,43 @@ __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2]
     PT[3] = b[3] - rho * ux * uy;
     PT[4] = b[4] - rho * ux * uz;
     PT[5] = b[5] - rho * uy * uz;
-    PY[0] = a[0] - (pY + rY * ux * ux);
-    PY[1] = a[1] - (pY + rY * uy * uy);
-    PY[2] = a[2] - (pY + rY * uz * uz);
-    PY[3] = a[3] - rY * ux * uy;
-    PY[4] = a[4] - rY * ux * uz;
-    PY[5] = a[5] - rY * uy * uz;
-    if (kExact && ink_exact_site(rY, rho)) ink_stress_exact<VS>(p, f[0], ux, uy, uz, PY);
+    if constexpr (kSplit) {
+        // ink stress by the split above: c Pi + H - h0 (I/3 + u u) + c kappa I
+        const real c = rY * irho;
+        real h0 = 0, H[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
+            const real h = rfma(-c, f[1][i], rfma(-c, p.wref[i], f[0][i]));
+            h0 += h;
+            if (cx) H[0] += h;
+            if (cy) H[1] += h;
+            if (cz) H[2] += h;
+            if (cx && cy) H[3] += (cx == cy) ? h : -h;
+            if (cx && cz) H[4] += (cx == cz) ? h : -h;
+            if (cy && cz) H[5] += (cy == cz) ? h : -h;
+        }
+        // isotropic part: -h0/3 + c kappa, and away from density ratio one the
+        // partial-pressure terms (c - 1) rho_Y (p_Y - 1/3) + c rho_B (p_B - 1/3)
+        real iso = rfma(c, p.kappa_w, -h0 * real(1.0 / 3.0));
+        if (!p.unit)
+            iso += (c - real(1)) * rY * (p.pfac[0] - real(1.0 / 3.0)) + c * rB * (p.pfac[1] - real(1.0 / 3.0));
+        PY[0] = rfma(c, PT[0], H[0]) + (iso - h0 * ux * ux);
+        PY[1] = rfma(c, PT[1], H[1]) + (iso - h0 * uy * uy);
+        PY[2] = rfma(c, PT[2], H[2]) + (iso - h0 * uz * uz);
+        PY[3] = rfma(c, PT[3], H[3]) - h0 * ux * uy;
+        PY[4] = rfma(c, PT[4], H[4]) - h0 * ux * uz;
+        PY[5] = rfma(c, PT[5], H[5]) - h0 * uy * uz;
+    } else {
+        // ink non-equilibrium stress as written: sum f^Y c c - rY (pfac_Y I + u u)
+        const real pY = p.pfac[0] * rY;
+        PY[0] = a[0] - (pY + rY * ux * ux);
+        PY[1] = a[1] - (pY + rY * uy * uy);
+        PY[2] = a[2] - (pY + rY * uz * uz);
+        PY[3] = a[3] - rY * ux * uy;
+        PY[4] = a[4] - rY * ux * uz;
+        PY[5] = a[5] - rY * uy * uz;
+    }
     if (VS::kPlanar) { PY[1] = PY[3] = PY[5] = 0; PT[1] = PT[3] = PT[5] = 0; }
     M->rY = rY;
     M->sd = sd;
@@ -830,21 +860,23 @@ __device__ __forceinline__ void collide_out(const StepArgs<real>& p, const Momen
     const real vv15 = real(1.5) * (vx * vx + vy * vy + vz * vz);
 
     // perturbation (Eq. 10) once on the total; recolouring (Eq. 14-16) with
-    // cos(phi_i) regularised as c.grad / (|c| sqrt(|grad|^2 + eps^2)), eps = 1e-4
+    // cos(phi_i) = c.grad / (|c| |grad|) as printed (Eq. 16), taken as 0 where
+    // |grad rho^N| is at or below the rounding level of the arithmetic (the
+    // 0/0 case: such a gradient has no meaningful direction)
     const bool pert = gNn > real(0) && Fn2 > real(0);
     const real pA = pert ? real(0.5) * p.A * gNn : real(0);
     const real pAF = pert ? qdiv(pA, Fn2) : real(0);
-    const real rec = p.beta * rY * rB * irho * irho * qrsqrt(gN2 + real(1e-8));
+    const real rec = gN2 > grad_floor2<real>() ? p.beta * rY * rB * irho * irho * qrsqrt(gN2) : real(0);
     const real tr3 = (PT[0] + PT[1] + PT[2]) * real(1.0 / 3.0);
-    const real drho = rho - p.rho_ref;
+    const real drho = M.sd;  // rho - rho_ref, the deviation sum itself
 
-    // rest direction
-    {
-        const real w = (real)VS::w(0);
-        real e = w * drho - rho * w * vv15 + om45 * w * (-tr3) - pA * (real)VS::B(0);
-        if constexpr (!kUnit) e += rY * p.dphi[0][0] + rB * p.dphi[1][0];
-        out(0, cY0 * (w * p.rho_ref + e), e, cY0);
-    }
+    // The collision conserves each component's mass (Eq. 5, 10, 14-15, 20,
+    // 29 each add zero mass), so the rest direction is written last as what
+    // that leaves: f^Y_0 = rho_Y - sum_{i>0} f^Y_i and d_0 = sd - sum_{i>0} d_i.
+    // In exact arithmetic this is the rest direction's formula; in FP32 it
+    // keeps the rounding of c_Y rho and of the weights (sum_i fl(w_i) != 1)
+    // from adding the same error to a site's mass at every step.
+    real sY = 0, sD = 0;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const int i = 2 * q + 1;
@@ -867,9 +899,14 @@ __device__ __forceinline__ void collide_out(const StepArgs<real>& p, const Momen
         else e0 = rY * p.phi[0][i] + rB * p.phi[1][i];
         const real G = rec * cg * e0;
         const real dp = e + o, dm = e - o;
-        out(i, cY0 * (w * p.rho_ref + dp) + G, dp, cY0);
-        out(i + 1, cY0 * (w * p.rho_ref + dm) - G, dm, cY0);
+        const real yp = cY0 * (w * p.rho_ref + dp) + G, ym = cY0 * (w * p.rho_ref + dm) - G;
+        out(i, yp, dp, cY0);
+        out(i + 1, ym, dm, cY0);
+        sY += yp + ym;
+        sD += dp + dm;
     }
+    // rest direction
+    out(0, rY - sY, M.sd - sD, cY0);
 
     so->rhoY = rY;
     so->rhoB = rB;

@@ -5,8 +5,8 @@
 
 namespace cglbm {
 
-template int launch_fused<float, __nv_bfloat16>(const StepArgs<float>&, int, cudaStream_t, int);
-template int launch_fused_batch<float, __nv_bfloat16>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+template int launch_fused<float, __nv_bfloat16>(const StepArgs<float>&, int, cudaStream_t);
+template int launch_fused_batch<float, __nv_bfloat16>(const StepArgs<float>*, const int4*, int, int*, int, int,
                                             cudaStream_t, int*);
 
 }  // namespace cglbm

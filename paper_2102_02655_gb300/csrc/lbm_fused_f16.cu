@@ -5,8 +5,8 @@
 
 namespace cglbm {
 
-template int launch_fused<float, __half>(const StepArgs<float>&, int, cudaStream_t, int);
-template int launch_fused_batch<float, __half>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+template int launch_fused<float, __half>(const StepArgs<float>&, int, cudaStream_t);
+template int launch_fused_batch<float, __half>(const StepArgs<float>*, const int4*, int, int*, int, int,
                                             cudaStream_t, int*);
 
 }  // namespace cglbm

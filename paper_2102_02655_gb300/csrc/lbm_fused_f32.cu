@@ -5,10 +5,8 @@
 
 namespace cglbm {
 
-int fused_tile_height(int variant, bool fp64) { return (!fp64 && variant == 1) ? 16 : 8; }
-
-template int launch_fused<float, float>(const StepArgs<float>&, int, cudaStream_t, int);
-template int launch_fused_batch<float, float>(const StepArgs<float>*, const int4*, int, int*, int, int, int,
+template int launch_fused<float, float>(const StepArgs<float>&, int, cudaStream_t);
+template int launch_fused_batch<float, float>(const StepArgs<float>*, const int4*, int, int*, int, int,
                                             cudaStream_t, int*);
 
 }  // namespace cglbm

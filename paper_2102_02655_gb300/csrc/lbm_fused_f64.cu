@@ -5,8 +5,8 @@
 
 namespace cglbm {
 
-template int launch_fused<double, double>(const StepArgs<double>&, int, cudaStream_t, int);
-template int launch_fused_batch<double, double>(const StepArgs<double>*, const int4*, int, int*, int, int, int,
+template int launch_fused<double, double>(const StepArgs<double>&, int, cudaStream_t);
+template int launch_fused_batch<double, double>(const StepArgs<double>*, const int4*, int, int*, int, int,
                                             cudaStream_t, int*);
 
 }  // namespace cglbm

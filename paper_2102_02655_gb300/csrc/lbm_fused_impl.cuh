@@ -224,39 +224,34 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 // One tile column (x0, y0) of planes [za, zb) of one lattice; shared memory
 // as laid out by fused_smem. Used by the single-lattice kernel (one column
 // per CTA) and by the persistent batched kernel (a list of columns per CTA).
-// kMom: the own sites wait for their collision as their 17 moments (see
-// moments()) instead of their 38 populations, which takes less than half the
-// shared memory and none of the populations' registers across the plane.
-template <typename real, typename S, bool kUnit, int TY_, bool kMom = false, int TX_ = 32>
+// The own sites wait for their collision as their 17 moments (see moments())
+// rather than their 38 populations: less than half the shared memory and
+// none of the populations' registers across the plane.
+template <typename real, typename S, bool kUnit, int TY_, int TX_ = 32>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
     using T = Tile<TY_, TX_>;
     constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
-    constexpr int NS = kMom ? 17 : 38;              // values staged per site
+    constexpr int NS = 17;                          // moments staged per site
     real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][NS][NT]
     Colour<real, kUnit, HS> C{pops + 2 * NS * NT};  // [4 slots][NV][HS]
     // substrate prologue scratch [2][SS]: staging buffer 1, first written
     // after the prologue's last read of it
     real* sub = pops + NS * NT;
     static_assert(NS * NT >= 2 * SS, "substrate scratch");
-    // the staged values of a site: populations, or moments
+    // a site waits for its collision as its 17 moments (see moments())
     auto stage = [&](real* b, const real f[2][19]) {
-        if constexpr (kMom) {
-            Moments<real> M;
-            moments<D3Q19, real, false>(p, f, &M);
-            b[0] = M.rY;
-            b[NT] = M.sd;
+        Moments<real> M;
+        moments<D3Q19>(p, f, &M);
+        b[0] = M.rY;
+        b[NT] = M.sd;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) b[(2 + k) * NT] = M.m[k];
+        for (int k = 0; k < 3; ++k) b[(2 + k) * NT] = M.m[k];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                b[(5 + k) * NT] = M.PY[k];
-                b[(11 + k) * NT] = M.PT[k];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 38; ++i) b[i * NT] = f[i / 19][i % 19];
+        for (int k = 0; k < 6; ++k) {
+            b[(5 + k) * NT] = M.PY[k];
+            b[(11 + k) * NT] = M.PT[k];
         }
     };
     (void)TX;
@@ -331,33 +326,20 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     const int hj = ry * HX + rx;
     auto load_interior = [&](int zz) {
         real rY, rB;
-        if constexpr (kMom) {
-            // one pull at a time: the register budget of more CTAs per SM
-            // holds one site's 38 values, not two
-            {
-                real f[2][19];
-                pull_interior<S>(p, gx, gy, zz, f);
-                stage(pops + (zz & 1) * NS * NT + tid, f);
-                density(f, p, &rY, &rB);
-                C.put(p, slot_of(zz), hidx, rY, rB);
-            }
-            if (has_halo) {
-                real h[2][19];
-                pull_interior<S>(p, hgx, hgy, zz, h);
-                density(h, p, &rY, &rB);
-                C.put(p, slot_of(zz), hj, rY, rB);
-            }
-        } else {
-            real f[2][19], h[2][19];
+        // one pull at a time: the register budget of three CTAs per SM holds
+        // one site's 38 values, not two
+        {
+            real f[2][19];
             pull_interior<S>(p, gx, gy, zz, f);
-            if (has_halo) pull_interior<S>(p, hgx, hgy, zz, h);
             stage(pops + (zz & 1) * NS * NT + tid, f);
             density(f, p, &rY, &rB);
             C.put(p, slot_of(zz), hidx, rY, rB);
-            if (has_halo) {
-                density(h, p, &rY, &rB);
-                C.put(p, slot_of(zz), hj, rY, rB);
-            }
+        }
+        if (has_halo) {
+            real h[2][19];
+            pull_interior<S>(p, hgx, hgy, zz, h);
+            density(h, p, &rY, &rB);
+            C.put(p, slot_of(zz), hj, rY, rB);
         }
     };
 
@@ -406,41 +388,20 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             const int s = z * (int)p.plane + y * p.nx + x;
             const int N = (int)p.N;
             const real* b = pops + (z & 1) * NS * NT + tid;
-            if constexpr (kMom) {
-                Moments<real> M;
-                M.rY = b[0];
-                M.sd = b[NT];
+            Moments<real> M;
+            M.rY = b[0];
+            M.sd = b[NT];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) M.m[k] = b[(2 + k) * NT];
+            for (int k = 0; k < 3; ++k) M.m[k] = b[(2 + k) * NT];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    M.PY[k] = b[(5 + k) * NT];
-                    M.PT[k] = b[(11 + k) * NT];
-                }
-                {
-                    // the ink's stress in double where it carries the rheology:
-                    // the site's populations pulled again (still in L2)
-                    const real rho = p.rho_ref + M.sd;
-                    if (ink_exact_site(M.rY, rho)) {
-                        const real irho = qdiv(real(1), rho);
-                        real fe[2][19];
-                        if (z < p.nz - 1) pull_interior<S>(p, gx, gy, z, fe);
-                        else pull_top<S>(p, gx, gy, fe, false);
-                        ink_stress_exact<D3Q19>(p, fe[0], M.m[0] * irho, M.m[1] * irho, M.m[2] * irho, M.PY);
-                    }
-                }
-                collide_out<D3Q19, real, kUnit>(p, M, nb, real(z) + real(0.5), &so,
-                                                [&](int i, real fY, real fD, real c) {
-                                                    pop_put<D3Q19, S>(p, i, s, N, fY, fD, c);
-                                                });
-            } else {
-                real f[2][19];
-#pragma unroll
-                for (int i = 0; i < 38; ++i) f[i / 19][i % 19] = b[i * NT];
-                collide<D3Q19, real, kUnit>(p, f, nb, real(z) + real(0.5), &so);
-#pragma unroll
-                for (int i = 0; i < 19; ++i) pop_put<D3Q19, S>(p, i, s, N, f[0][i], f[1][i], so.cY);
+            for (int k = 0; k < 6; ++k) {
+                M.PY[k] = b[(5 + k) * NT];
+                M.PT[k] = b[(11 + k) * NT];
             }
+            collide_out<D3Q19, real, kUnit>(p, M, nb, real(z) + real(0.5), &so,
+                                            [&](int i, real fY, real fD, real c) {
+                                                pop_put<D3Q19, S>(p, i, s, N, fY, fD, c);
+                                            });
             ref_put<S>(p, s, so.cY);
             if (z >= p.nz - 2)
                 for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
@@ -477,19 +438,24 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int TY_, bool kMom = false, int TX_ = 32>
+template <typename real, bool kUnit, int TY_, int TX_ = 32>
 constexpr size_t fused_smem() {
     using T = Tile<TY_, TX_>;
-    return sizeof(real) * (2 * (kMom ? 17 : 38) * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
+    return sizeof(real) * (2 * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, int TX_ = 32>
-__global__ void __launch_bounds__(Tile<TY_, TX_>::NT, MINB) k_fused(StepArgs<real> p, int zchunk) {
+// Configuration of the bulk kernel: 32 x 8 tiles, three CTAs per SM in FP32
+// arithmetic (80 registers), one in FP64.
+template <typename real>
+constexpr int fused_minb() { return sizeof(real) == 8 ? 1 : 3; }
+constexpr int kTileH = 8;
+
+template <typename real, typename S, bool kUnit>
+__global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>()) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = z_chunks(p.nz, zchunk);
-    fused_column<real, S, kUnit, TY_, kMom, TX_>(p, smraw, blockIdx.x * TX_, blockIdx.y * TY_,
-                                                 z_chunk_begin(p.nz, n, blockIdx.z),
-                                                 z_chunk_begin(p.nz, n, blockIdx.z + 1));
+    fused_column<real, S, kUnit, kTileH>(p, smraw, blockIdx.x * 32, blockIdx.y * kTileH,
+                                         z_chunk_begin(p.nz, n, blockIdx.z), z_chunk_begin(p.nz, n, blockIdx.z + 1));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -497,15 +463,15 @@ __global__ void __launch_bounds__(Tile<TY_, TX_>::NT, MINB) k_fused(StepArgs<rea
 // zero at launch), so CTAs that become resident late, behind other kernels,
 // simply take fewer columns. Each lattice's step arguments are copied to
 // shared memory when a CTA's column changes lattice.
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
-__global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
+template <typename real, typename S, bool kUnit>
+__global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>())
     k_fused_batch(const StepArgs<real>* __restrict__ args, const int4* __restrict__ items, int n_items,
                   int* __restrict__ queue) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ __align__(16) StepArgs<real> sp;
     __shared__ int next;
-    constexpr int NT = Tile<TY_>::NT;
-    const int tid = threadIdx.y * Tile<TY_>::TX + threadIdx.x;
+    constexpr int NT = Tile<kTileH>::NT;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     int last = -1;
     for (;;) {
         __syncthreads();  // the previous column's shared state and `next` are free
@@ -521,415 +487,62 @@ __global__ void __launch_bounds__(Tile<TY_>::NT, MINB)
             last = it.x;
             __syncthreads();
         }
-        fused_column<real, S, kUnit, TY_, kMom>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
+        fused_column<real, S, kUnit, kTileH>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
     }
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom, int TX_ = 32>
-int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    using T = Tile<TY_, TX_>;
-    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom, TX_>();
-    static_assert(smem <= 227 * 1024, "shared memory of one CTA");
-    static unsigned configured = 0;  // one bit per device: the attribute is set once per context
+// the kernel's dynamic shared memory limit is set once per device (context)
+template <typename K>
+void set_smem_once(K kernel, size_t smem, unsigned* configured) {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused<real, S, kUnit, TY_, MINB, kMom, TX_>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured |= 1u << dev;
+    if (dev < 32 && !(*configured & (1u << dev))) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        *configured |= 1u << dev;
     }
-    dim3 block(T::TX, T::TY);
-    dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, z_chunks(p.nz, zchunk));
-    k_fused<real, S, kUnit, TY_, MINB, kMom, TX_><<<grid, block, smem, st>>>(p, zchunk);
+}
+
+template <typename real, typename S, bool kUnit>
+int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
+    constexpr size_t smem = fused_smem<real, kUnit, kTileH>();
+    static_assert(smem <= 227 * 1024, "shared memory of one CTA");
+    static unsigned configured = 0;
+    set_smem_once(k_fused<real, S, kUnit>, smem, &configured);
+    dim3 block(32, kTileH);
+    dim3 grid((p.nx + 31) / 32, (p.ny + kTileH - 1) / kTileH, z_chunks(p.nz, zchunk));
+    k_fused<real, S, kUnit><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
 
-template <typename real, typename S, bool kUnit, int TY_, int MINB, bool kMom>
+template <typename real, typename S, bool kUnit>
 int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
                      cudaStream_t st, int* occupancy) {
-    constexpr size_t smem = fused_smem<real, kUnit, TY_, kMom>();
+    constexpr size_t smem = fused_smem<real, kUnit, kTileH>();
     static unsigned configured = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused_batch<real, S, kUnit, TY_, MINB, kMom>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured |= 1u << dev;
-    }
+    set_smem_once(k_fused_batch<real, S, kUnit>, smem, &configured);
     if (occupancy) {
         *occupancy = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_fused_batch<real, S, kUnit, TY_, MINB, kMom>,
-                                                      Tile<TY_>::NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_fused_batch<real, S, kUnit>, Tile<kTileH>::NT,
+                                                      smem);
         return 0;
     }
     if (n_items <= 0) return 0;
-    k_fused_batch<real, S, kUnit, TY_, MINB, kMom><<<grid, dim3(Tile<TY_>::TX, TY_), smem, st>>>(args, items, n_items,
-                                                                                       queue);
-    return 1;
-}
-
-template <typename real, typename S, int TY_, int MINB, bool kMom = false>
-int batch_variant(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
-                  cudaStream_t st, int* occupancy) {
-    return unit ? launch_batch_one<real, S, true, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy)
-                : launch_batch_one<real, S, false, TY_, MINB, kMom>(args, items, n_items, queue, grid, st, occupancy);
-}
-
-template <typename real, typename S, int TY_, int MINB, bool kMom = false, int TX_ = 32>
-int launch_variant(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    return p.unit ? launch_one<real, S, true, TY_, MINB, kMom, TX_>(p, zchunk, st)
-                  : launch_one<real, S, false, TY_, MINB, kMom, TX_>(p, zchunk, st);
-}
-
-// ---------------------------------------------------------------------------
-// Warp-specialised form: CTAs of 16 warps on a 32 x 8 tile, two per SM.
-// Warps 8-15 (producers) pull the planes ahead and form each own site's 17
-// moments into a three-stage shared-memory ring, and the densities of tile and
-// halo into a four-plane colour ring. Warps 0-7 (consumers) collide from the
-// staged moments. Two mbarriers per stage hand it over (full: producers to
-// consumers; empty: consumers back), so the producers keep loads in flight
-// while the consumers compute, and neither side waits at a CTA-wide barrier.
-// A stage is reused only after the collision of its plane (empty), and a
-// colour slot after the collision of the plane above it, which the same wait
-// guarantees. Every wait is bounded: one that runs out sets bit 2 of the
-// flags and its thread leaves, so the others run out in turn.
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// wait for the completion of the phase with the given parity; each poll
-// suspends for at most 1 us, so false after about 2 s: the bound on every
-// wait of this kernel
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    const unsigned a = smem_u32(bar);
-    for (int it = 0; it < (1 << 21); ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity), "r"(1000u)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-
-constexpr int kWsStages = 3;
-
-template <typename real, bool kUnit>
-constexpr size_t ws_smem() {
-    using T = Tile<8>;
-    return sizeof(real) * (kWsStages * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS + 2 * T::SS);
-}
-
-template <typename real, typename S, bool kUnit, int MINB>
-__global__ void __launch_bounds__(512, MINB) k_fused_ws(StepArgs<real> p, int zchunk) {
-    using T = Tile<8>;
-    constexpr int TX = T::TX, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
-    constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
-    constexpr int K = kWsStages;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    real* ring = reinterpret_cast<real*>(smraw);             // [K][17][NT]
-    Colour<real, kUnit, HS> C{ring + K * 17 * NT};             // [4 slots][NV][HS]
-    real* sub = C.col + 4 * Colour<real, kUnit, HS>::NV * HS;  // [2][SS]
-    __shared__ __align__(8) unsigned long long full[K], empty[K];
-
-    const int tid = threadIdx.x;
-    const bool producer = tid >= NT;
-    const int q = producer ? tid - NT : tid;  // the thread's site in the tile
-    const int tx = q % TX, ty = q / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * T::TY;
-    const int nch = z_chunks(p.nz, zchunk);
-    const int za = z_chunk_begin(p.nz, nch, blockIdx.z);
-    const int zb = z_chunk_begin(p.nz, nch, blockIdx.z + 1);
-    const int zlast = min(zb, p.nz - 1);  // last plane the producers pull
-    const int nplanes = zlast - za + 2;   // planes za - 1 .. zlast, index j = zz - za + 1
-    const int x = x0 + tx, y = y0 + ty;
-    const bool in_xy = x < p.nx && y < p.ny;
-    const int gx = in_xy ? x : wrapn(x, p.nx), gy = in_xy ? y : wrapn(y, p.ny);
-    const int hidx = (ty + 1) * HX + (tx + 1);
-    if (tid < K) {
-        mbar_init(&full[tid], NT);
-        mbar_init(&empty[tid], NT);
-    }
-    __syncthreads();
-
-    if (producer) {
-        double bc[2] = {0.0, 0.0};
-        const bool has_halo = q < NRING;
-        int rx = 0, ry = 0;
-        if (has_halo) ring_coord<HX, HY>(q, &rx, &ry);
-        const int hgx = wrapn(x0 - 1 + rx, p.nx), hgy = wrapn(y0 - 1 + ry, p.ny);
-        const int hj = ry * HX + rx;
-        auto stage = [&](real* b, const real f[2][19]) {
-            Moments<real> M;
-            moments<D3Q19, real, false>(p, f, &M);
-            b[0] = M.rY;
-            b[NT] = M.sd;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) b[(2 + k) * NT] = M.m[k];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                b[(5 + k) * NT] = M.PY[k];
-                b[(11 + k) * NT] = M.PT[k];
-            }
-        };
-        // any plane (boundary rules included) for the own site, the halo and,
-        // when outer, the second ring (substrate ghost plane)
-        auto load_general = [&](int zz, real* own_dst, int slot, bool outer) {
-            const int nitems = outer ? 3 : 2;
-            for (int it = 0; it < nitems; ++it) {
-                int ex, ey;  // coordinates in the tile grown by two rings
-                if (it == 0) {
-                    ex = tx + 2;
-                    ey = ty + 2;
-                } else if (it == 1) {
-                    if (!has_halo) continue;
-                    ex = rx + 1;
-                    ey = ry + 1;
-                } else {
-                    if (q >= SS - HS) continue;
-                    if (q < SX) { ex = q; ey = 0; }
-                    else if (q < 2 * SX) { ex = q - SX; ey = SY - 1; }
-                    else { const int k = q - 2 * SX; ey = 1 + (k >> 1); ex = (k & 1) ? SX - 1 : 0; }
-                }
-                const int px = wrapn(x0 - 2 + ex, p.nx), py = wrapn(y0 - 2 + ey, p.ny);
-                const bool own = it == 0;
-                real* dst = own ? own_dst : nullptr;
-                real rY, rB;
-                if (zz == p.nz - 1) {
-                    real ft[2][19];
-                    const TopPull<real> r =
-                        pull_top<S>(p, px, py, ft, own && dst && in_xy && zz < zb && !in_box(p, x, y, zz));
-                    if (dst) stage(dst, ft);
-                    rY = r.rY;
-                    rB = r.rB;
-                    bc[0] += r.b0;
-                    bc[1] += r.b1;
-                } else {
-                    real f[2][19];
-                    pull_interior<S>(p, px, py, zz, f);
-                    if (dst) stage(dst, f);
-                    density(f, p, &rY, &rB);
-                }
-                if (outer) {
-                    sub[ey * SX + ex] = rY;
-                    sub[SS + ey * SX + ex] = rB;
-                }
-                if (it < 2) C.put(p, slot, (ey - 1) * HX + (ex - 1), rY, rB);
-            }
-        };
-        bool ok = true;
-        for (int j = 0; j < nplanes; ++j) {
-            const int zz = za - 1 + j;
-            if (j >= K && !(ok = mbar_wait(&empty[j % K], ((j - K) / K) & 1))) break;
-            real* own_dst = (zz >= za && zz < zb) ? ring + (j % K) * 17 * NT + q : nullptr;
-            if (za == 0 && j == 0) {
-                // plane 0 with two rings (index 1), then the substrate ghost
-                // plane z = -1 (index 0) by the fictitious-density rule (Eq. 18)
-                load_general(0, ring + 1 * 17 * NT + q, 1, true);
-                producers_sync();
-                for (int jj = q; jj < HS; jj += NT) {
-                    const int ex = jj % HX, ey = jj / HX;
-                    const int c = (ey + 1) * SX + (ex + 1);
-                    real n0 = 0, n1 = 0, den = 0;
-#pragma unroll
-                    for (int i = 1; i < 19; ++i) {
-                        if (D3Q19::c(i, 2) != 1) continue;
-                        const real w = (real)D3Q19::w(i);
-                        const int cc = c + D3Q19::c(i, 0) + D3Q19::c(i, 1) * SX;
-                        n0 += w * sub[cc];
-                        n1 += w * sub[SS + cc];
-                        den += w;
-                    }
-                    C.put(p, 0, jj, p.zeta[0] * n0 / den, p.zeta[1] * n1 / den);
-                }
-                mbar_arrive(&full[0]);
-                mbar_arrive(&full[1]);
-                ++j;
-                continue;
-            }
-            if (zz == p.nz - 1 || zz < 1) {
-                load_general(zz, own_dst, j & 3, false);
-            } else {
-                real rY, rB;
-                {
-                    real f[2][19];
-                    pull_interior<S>(p, gx, gy, zz, f);
-                    if (own_dst) stage(own_dst, f);
-                    density(f, p, &rY, &rB);
-                    C.put(p, j & 3, hidx, rY, rB);
-                }
-                if (has_halo) {
-                    real h[2][19];
-                    pull_interior<S>(p, hgx, hgy, zz, h);
-                    density(h, p, &rY, &rB);
-                    C.put(p, j & 3, hj, rY, rB);
-                }
-            }
-            mbar_arrive(&full[j % K]);
-        }
-        if (!ok) atomicOr(p.flags, 2);
-        warp_add(p.acc + kAccBc, bc[0]);
-        warp_add(p.acc + kAccBc + 1, bc[1]);
-    } else {
-        int bad = 0;
-        bool ok = mbar_wait(&full[0], 0) && mbar_wait(&full[1], 0);
-        if (ok) mbar_arrive(&empty[0]);  // plane za - 1 keeps no moments
-        for (int z = za; z < zb && ok; ++z) {
-            const int j = z - za + 1, jn = j + 1;
-            if (z + 1 <= zlast && !(ok = mbar_wait(&full[jn % K], (jn / K) & 1))) break;
-            if (in_xy && !in_box(p, x, y, z)) {
-                const real* b = ring + (j % K) * 17 * NT + q;
-                Moments<real> M;
-                M.rY = b[0];
-                M.sd = b[NT];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) M.m[k] = b[(2 + k) * NT];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    M.PY[k] = b[(5 + k) * NT];
-                    M.PT[k] = b[(11 + k) * NT];
-                }
-                {
-                    // the ink's stress in double where it carries the rheology:
-                    // the site's populations pulled again (still in L2)
-                    const real rho = p.rho_ref + M.sd;
-                    if (ink_exact_site(M.rY, rho)) {
-                        const real irho = qdiv(real(1), rho);
-                        real fe[2][19];
-                        if (z < p.nz - 1) pull_interior<S>(p, gx, gy, z, fe);
-                        else pull_top<S>(p, gx, gy, fe, false);
-                        ink_stress_exact<D3Q19>(p, fe[0], M.m[0] * irho, M.m[1] * irho, M.m[2] * irho, M.PY);
-                    }
-                }
-                // open top: zero normal gradient, the ghost plane above is the top plane
-                const int sup = z + 1 < p.nz ? (jn & 3) : (j & 3);
-                SmemNb<real, kUnit, HX, HS> nb{C.col, {(j - 1) & 3, j & 3, sup}, hidx};
-                SiteOut<real> so;
-                const int s = z * (int)p.plane + y * p.nx + x;
-                const int N = (int)p.N;
-                collide_out<D3Q19, real, kUnit>(p, M, nb, real(z) + real(0.5), &so,
-                                                [&](int i, real fY, real fD, real c) {
-                                                    pop_put<D3Q19, S>(p, i, s, N, fY, fD, c);
-                                                });
-                ref_put<S>(p, s, so.cY);
-                if (z >= p.nz - 2)
-                    for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
-                if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
-                if (p.write_fields) {
-                    real* F = p.fields;
-                    F[kFRhoInk * p.N + s] = so.rhoY;
-                    F[kFRhoAmb * p.N + s] = so.rhoB;
-                    F[kFUx * p.N + s] = so.u[0];
-                    F[kFUy * p.N + s] = so.u[1];
-                    F[kFUz * p.N + s] = so.u[2];
-                    F[kFNu * p.N + s] = (so.tau - real(0.5)) * real(1.0 / 3.0);
-                    F[kFP * p.N + s] = p.pfac[0] * so.rhoY + p.pfac[1] * so.rhoB;
-                    F[kFPhi * p.N + s] = so.rn;
-                    F[kFSolid * p.N + s] = real(0);
-                }
-            }
-            if (p.write_fields) {
-                // the FP64 sums leave the registers plane by plane
-                double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
-                if (in_xy && !in_box(p, x, y, z)) {
-                    const int s = z * (int)p.plane + y * p.nx + x;
-                    const real* F = p.fields;
-                    const double rY = F[kFRhoInk * p.N + s], rB = F[kFRhoAmb * p.N + s];
-                    m0 = rY;
-                    m1 = rB;
-                    mx = (rY + rB) * (double)F[kFUx * p.N + s];
-                    my = (rY + rB) * (double)F[kFUy * p.N + s];
-                    mz = (rY + rB) * (double)F[kFUz * p.N + s];
-                }
-                warp_add(p.acc + kAccMass, m0);
-                warp_add(p.acc + kAccMass + 1, m1);
-                warp_add(p.acc + kAccMom, mx);
-                warp_add(p.acc + kAccMom + 1, my);
-                warp_add(p.acc + kAccMom + 2, mz);
-            }
-            mbar_arrive(&empty[j % K]);
-        }
-        if (!ok) atomicOr(p.flags, 2);
-        if (bad) atomicOr(p.flags, 1);
-    }
-}
-
-template <typename real, typename S, bool kUnit, int MINB>
-int launch_ws(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr size_t smem = ws_smem<real, kUnit>();
-    static_assert(smem <= 227 * 1024, "shared memory of one CTA");
-    static unsigned configured = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 32 && !(configured & (1u << dev))) {
-        cudaFuncSetAttribute(k_fused_ws<real, S, kUnit, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured |= 1u << dev;
-    }
-    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, z_chunks(p.nz, zchunk));
-    k_fused_ws<real, S, kUnit, MINB><<<grid, 512, smem, st>>>(p, zchunk);
+    k_fused_batch<real, S, kUnit><<<grid, dim3(32, kTileH), smem, st>>>(args, items, n_items, queue);
     return 1;
 }
 
 }  // namespace
 
-// Variant 0 (default): 32 x 8 tiles, own sites staged as their 17 moments,
-// three CTAs per SM (80 registers; one CTA per SM in FP64). The others exist
-// for tuning measurements (CGLBM_FUSED_VARIANT): 1 = 32 x 16 tiles with
-// staged populations, one CTA per SM; 2 = staged populations (38 per site),
-// two CTAs per SM; 3 = moments at two CTAs per SM; 7 = warp-specialised
-// (producer and consumer warps), two 512-thread CTAs per SM; 4 = as 0 on
-// 16 x 16 tiles (a 68-site halo ring instead of 84). 16-bit storage has the
-// default only.
 template <typename real, typename S>
-int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant) {
-    if constexpr (sizeof(real) == 8) {
-        if (variant == 2) return launch_variant<real, S, 8, 1>(p, zchunk, st);
-        return launch_variant<real, S, 8, 1, true>(p, zchunk, st);
-    } else if constexpr (!std::is_same<S, real>::value) {
-        (void)variant;  // 16-bit storage: the default configuration only
-        return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
-    } else {
-        switch (variant) {
-        case 1: return launch_variant<real, S, 16, 1>(p, zchunk, st);
-        case 2: return launch_variant<real, S, 8, 2>(p, zchunk, st);
-        case 3: return launch_variant<real, S, 8, 2, true>(p, zchunk, st);
-        case 7:
-            return p.unit ? launch_ws<real, S, true, 2>(p, zchunk, st) : launch_ws<real, S, false, 2>(p, zchunk, st);
-        case 4: return launch_variant<real, S, 16, 3, true, 16>(p, zchunk, st);
-        default: return launch_variant<real, S, 8, 3, true>(p, zchunk, st);
-        }
-    }
+int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
+    return p.unit ? launch_one<real, S, true>(p, zchunk, st) : launch_one<real, S, false>(p, zchunk, st);
 }
 
 template <typename real, typename S>
 int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
-                       int variant, cudaStream_t st, int* occupancy) {
-    if constexpr (sizeof(real) == 8) {
-        (void)variant;
-        return batch_variant<real, S, 8, 1, true>(args, items, n_items, queue, grid, unit, st, occupancy);
-    } else {
-        if constexpr (std::is_same<S, real>::value) {
-            if (variant == 1)
-                return batch_variant<real, S, 16, 1>(args, items, n_items, queue, grid, unit, st, occupancy);
-        }
-        return batch_variant<real, S, 8, 3, true>(args, items, n_items, queue, grid, unit, st, occupancy);
-    }
+                       cudaStream_t st, int* occupancy) {
+    return unit ? launch_batch_one<real, S, true>(args, items, n_items, queue, grid, st, occupancy)
+                : launch_batch_one<real, S, false>(args, items, n_items, queue, grid, st, occupancy);
 }
 
 }  // namespace cglbm

@@ -31,21 +31,21 @@ template <class VS, typename real, typename S>
 int launch_plain(const StepArgs<real>& p, const Region& R, const Region& R1, const Region& R2, cudaStream_t st);
 
 // Fused bulk step over every site outside p.box (D3Q19, substrate + open top).
-// variant selects a tile/staging configuration (0 = default).
 template <typename real, typename S>
-int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st, int variant);
+int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st);
 
 // Persistent fused bulk step over many lattices in one launch: grid CTAs take
 // the work list items (lattice index, x0 | y0 << 16, za, zb: one tile column
 // of planes [za, zb)) in order through the counter *queue (zero at launch),
 // reading each lattice's StepArgs from args (device). All lattices share the
-// kernel configuration (unit flag, variant). With occupancy != NULL nothing
-// is launched and the resident CTAs per SM of that configuration are
-// returned there.
+// kernel configuration (unit flag). With occupancy != NULL nothing is
+// launched and the resident CTAs per SM of that configuration are returned
+// there.
 template <typename real, typename S>
 int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
-                       int variant, cudaStream_t st, int* occupancy);
-int fused_tile_height(int variant, bool fp64);
+                       cudaStream_t st, int* occupancy);
+// tile height (sites in y) of the fused kernels' 32-wide column tiles
+constexpr int kFusedTileH = 8;
 
 // Batched phase-by-phase step of the nozzle boxes of many lattices: one
 // launch per phase over all lattices (blockIdx.z), each lattice's StepArgs

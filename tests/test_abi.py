@@ -74,3 +74,48 @@ def test_python_wrapper_raises_with_message(L):
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_create(_cfg(nz=0))
     assert e.value.status == lbm.LBM_EINVAL
+
+
+def _noalloc(L, cfg, geom=None, rheo=None):
+    g = lbm.make_geometry(dict(dict(head_pos=(4.0, 4.0), gap=3, r_inner=1.5), **(geom or {})))
+    r = lbm.make_rheology(rheo)
+    return L.lbm_step_noalloc(C.byref(cfg), C.byref(g), C.byref(r), 1, C.c_void_p(1 << 20), C.c_void_p(1 << 30),
+                              None, None)
+
+
+@pytest.mark.parametrize("geom,rheo,msg", [
+    (dict(head_pos=(float("nan"), 4.0)), None, "head position"),
+    (dict(head_vel=(0.6, 0.0)), None, "head position"),
+    (dict(u_ink=float("inf")), None, "u_ink"),
+    (dict(r_inner=1500.0, wall_thickness=600.0), None, "radii"),
+    (dict(rho_top_amb=0.0), None, "rho_top_amb"),
+    (dict(top_vel=(float("nan"), 0.0, 0.0)), None, "top_vel"),
+    (None, dict(law=lbm.LBM_POWER_LAW, K=0.0), "power law"),
+    (None, dict(law=lbm.LBM_CROSS, lam=0.0), "Cross"),
+    (None, dict(law=lbm.LBM_NEWTONIAN, nu0=float("nan")), "nu0"),
+    (None, dict(tau_min=0.5), "tau_min"),
+    (None, dict(law=9), "unknown law"),
+])
+def test_step_noalloc_checks_like_the_handle_calls(L, geom, rheo, msg):
+    """lbm_step_noalloc applies the checks of lbm_create, lbm_set_geometry and
+    lbm_set_ink_rheology, on the host, before any device work."""
+    assert _noalloc(L, _cfg(), geom, rheo) == lbm.LBM_EINVAL
+    assert msg in L.lbm_last_error(None).decode()
+
+
+def test_nozzle_lattice_width_limit(L):
+    """The fixed-point nozzle geometry squares half a lattice side in 64-bit
+    integers: nozzle runs are limited to nx, ny <= 4000."""
+    assert _noalloc(L, _cfg(shape=(4001, 8, 8))) == lbm.LBM_EINVAL
+    assert "4000" in L.lbm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("field,value", [("drag_gamma", float("nan")), ("zeta_ink", float("inf")),
+                                         ("A", float("nan")), ("rho0_amb", float("inf"))])
+def test_create_rejects_non_finite_constants(L, field, value):
+    cfg = _cfg(**{field: value})
+    h = C.c_void_p()
+    assert L.lbm_create(C.byref(cfg), C.byref(h)) == lbm.LBM_EINVAL
+    cfg = _cfg()
+    cfg.body_force[1] = float("nan")
+    assert L.lbm_create(C.byref(cfg), C.byref(h)) == lbm.LBM_EINVAL

@@ -3,15 +3,13 @@ the same seeded inputs, field by field.
 
 Error measure: for each macroscopic field, max |gpu - oracle| / max |oracle|
 (the field's own scale; the speed for velocity components). Bars: FP64
-storage 1e-12, FP32 storage 1e-5 on the hydrodynamic fields (densities,
-velocity, pressure, phase field). The local viscosity nu is evaluated from the
-non-equilibrium stress, a quantity 10^-2..10^-3 the size of the populations it
-is computed from, so it amplifies population differences: its FP32 bar is
-5e-5, and for the Cross law (unbounded slope at zero shear) the FP64 bar adds
-the bound of cross_nu_floor. The phase field rho^N = 2 rho_Y/rho - 1 (density
-ratio one) doubles the colour-fraction error: its bar is twice the density bar. FP32 errors grow with simulated time (velocity
-round-off integrates into interface displacement): FP32 runs are compared at a
-200-step horizon, and the drift to 500 steps is bounded separately."""
+storage 1e-12 and FP32 storage 1e-5, on every field (densities, velocity,
+local viscosity, pressure, phase field). The one allowance is the Cross law
+with n < 1 in FP64: its slope is unbounded at zero shear, so two correct
+evaluations of nu at nearly resting ink differ by up to the bound of
+cross_nu_floor (a property of the law, below 1e-8 in the case tested). The
+oracle compared with a path that computes in FP32 takes FP32's rounding floor
+for the direction of Eq. 16 (see oracle.grad_floor)."""
 import numpy as np
 import pytest
 
@@ -22,7 +20,6 @@ pytestmark = pytest.mark.gpu
 
 FIELDS = ("rho_ink", "rho_amb", "ux", "uy", "uz", "nu", "p", "rhoN")
 TOL = {"f64": 1e-12, "f32": 1e-5}
-NU_TOL = {"f64": 1e-12, "f32": 5e-5}
 
 
 def _lbm():
@@ -60,13 +57,8 @@ def cross_nu_floor(rheo, eps):
 
 def assert_close(fg, fo, tol, names=FIELDS, label="", nu_tol=None):
     errs = field_errors(fg, fo, names)
-    if nu_tol is None:
-        nu_tol = NU_TOL["f32"] if tol >= TOL["f32"] else tol
-    if "nu" in errs and errs["nu"] <= nu_tol:
+    if nu_tol is not None and "nu" in errs and errs["nu"] <= nu_tol:
         errs["nu"] = 0.0
-    # rho^N = 2 rho_Y/rho - 1 at density ratio one: twice the colour-fraction error
-    if "rhoN" in errs and errs["rhoN"] <= 2 * tol:
-        errs["rhoN"] = 0.0
     bad = {k: v for k, v in errs.items() if not (v <= tol)}
     assert not bad, "%s: fields over %.1e: %s" % (label, tol, {k: "%.3e" % v for k, v in bad.items()})
     # solid flags are integers: bit-exact
@@ -109,25 +101,32 @@ def run_pair(shape, wl, steps, path, storage=None, init=None, seed=1):
 
 @pytest.fixture(scope="module")
 def small_print_oracle():
+    """The 64x32x32 print run on the oracle to 100, 200 and 500 steps, twice:
+    with the FP64 rounding floor of Eq. 16's direction (for the FP64 path) and
+    with the FP32 one (for the paths that compute in FP32)."""
     wl = I.workload("small_print_f64")
     shape = wl["shape"]
     rY, rB = I.nozzle_fill(shape, wl["geom"])
     rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=0))
-    ref = O.Oracle(shape, params=wl["params"], geom=wl["geom"], rheo=wl["rheo"])
-    ref.set_fields(rY, rB)
-    snaps = {}
-    done = 0
-    for n in (100, 200, 500):
-        ref.step(n - done)
-        done = n
-        snaps[n] = (ref.fields(), ref.diag())
-    return wl, (rY, rB), snaps
+    out = {}
+    for st in ("f64", "f32"):
+        ref = O.Oracle(shape, params=dict(wl["params"], storage=st), geom=wl["geom"], rheo=wl["rheo"])
+        ref.set_fields(rY, rB)
+        snaps = {}
+        done = 0
+        for n in (100, 200, 500):
+            ref.step(n - done)
+            done = n
+            snaps[n] = (ref.fields(), ref.diag())
+        out[st] = snaps
+    return wl, (rY, rB), out
 
 
 @pytest.mark.parametrize("path", ["plain", "fused"])
 def test_small_print_f64_500_steps(small_print_oracle, path):
     lbm = _lbm()
-    wl, init, snaps = small_print_oracle
+    wl, init, runs = small_print_oracle
+    snaps = runs["f64"]
     lat = lbm.Lattice(wl["shape"], wl["params"], wl["geom"], wl["rheo"], path=path)
     lat.set_fields(*init)
     done = 0
@@ -145,19 +144,19 @@ def test_small_print_f64_500_steps(small_print_oracle, path):
 
 
 def test_small_print_f32(small_print_oracle):
+    """FP32 storage and arithmetic over the 64x32x32 print run's 500 steps, at
+    the FP32 bar (1e-5) at every horizon."""
     lbm = _lbm()
-    wl, init, snaps = small_print_oracle
+    wl, init, runs = small_print_oracle
+    snaps = runs["f32"]
     params = dict(wl["params"], storage="f32")
     lat = lbm.Lattice(wl["shape"], params, wl["geom"], wl["rheo"], path="fused")
     lat.set_fields(*init)
-    lat.step(100)
-    assert_close(lat.fields(), snaps[100][0], TOL["f32"], label="f32 fused step 100")
-    lat.step(100)
-    assert_close(lat.fields(), snaps[200][0], TOL["f32"], label="f32 fused step 200")
-    lat.step(300)
-    errs = field_errors(lat.fields(), snaps[500][0])
-    # drift bound at 500 steps (the error grows about linearly with time)
-    assert max(errs.values()) < 3e-5, errs
+    done = 0
+    for n in (100, 200, 500):
+        lat.step(n - done)
+        done = n
+        assert_close(lat.fields(), snaps[n][0], TOL["f32"], label="f32 fused step %d" % n)
     lat.close()
 
 
@@ -250,21 +249,19 @@ def test_tiny_lattices():
 
 
 def test_degenerate_symmetric_mixed_layer():
-    """A mixed layer whose colour gradient vanishes by symmetry at its centre:
-    the recolouring direction there is rounding noise on both sides, bounded by
-    the regularised cos(phi) to ~1e-16/1e-4 per step (without the
-    regularisation the two sides differ at O(1) after two steps). A uniform
-    mixture is unstable under recolouring (it separates and amplifies any
-    asymmetry by about e^1.7 per step here), so the comparison covers the first
-    five steps, with the bar 1e-6."""
+    """A mixed layer whose colour gradient vanishes by symmetry at its centre.
+    There the computed gradient is rounding noise (or exactly zero), below the
+    floor under which Eq. 16's direction is undefined, so neither side
+    recolours it in a noise direction, and both follow the same symmetric
+    evolution: 30 steps at the FP64 bar."""
     shape = (1, 1, 5)
     rY = np.zeros((5, 1, 1))
     rY[2] = 0.5
     wl = dict(params=dict(velset=1, storage="f64"), geom=dict(nozzle=0, z_mode=O.Z_PERIODIC),
               rheo=dict(law=O.POWER_LAW, n=0.6, K=0.05, tau_min=0.51, tau_max=2.0))
     for path in ("plain", "auto"):
-        fg, fo, _ = run_pair(shape, wl, 5, path, init=(rY, 1.0 - rY))
-        assert_close(fg, fo, 1e-6, label="symmetric layer %s" % path)
+        fg, fo, _ = run_pair(shape, wl, 30, path, init=(rY, 1.0 - rY))
+        assert_close(fg, fo, TOL["f64"], label="symmetric layer %s" % path)
 
 
 # ---------------------------------------------------------------------------
@@ -378,7 +375,7 @@ def test_full_size_print_f32_against_oracle():
     fg = lat.fields()
     d = lat.diag()
     lat.close()
-    ref = O.Oracle(shape, params=dict(wl["params"], storage="f64"), geom=wl["geom"], rheo=wl["rheo"])
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f32"), geom=wl["geom"], rheo=wl["rheo"])
     ref.set_fields(rY, rB)
     ref.step(3)
     fo = ref.fields()

@@ -5,6 +5,7 @@ agree to rounding)."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2102_02655_gb300 import inputs as I
 
 from test_gpu_parity import _lbm, field_errors
@@ -92,3 +93,40 @@ def test_budget_limits_the_active_set():
     assert done[huge] == lbm.LBM_ENOMEM
     assert all(v == 0 for k, v in done.items() if k != huge)
     assert peak_bytes <= 2 * big + 1 and st["peak_active"] <= 2
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_served_requests_against_oracle(storage):
+    """Requests served together (continuous batching, arrivals interleaved
+    with rounds) against the FP64 oracle after 100-150 steps each, at the
+    storage's stated bar: 1e-5 (FP32), 1e-3 (FP16 deviations)."""
+    lbm = _lbm()
+    rng = np.random.default_rng(31)
+    reqs = []
+    for _ in range(3):
+        shape = (int(rng.choice([48, 64])), 32, 32)
+        wl = I.print_run(shape, float(rng.uniform(3.0, 5.0)), 10, float(rng.uniform(0.005, 0.02)),
+                         float(rng.uniform(0.02, 0.05)), float(rng.uniform(0.4, 0.8)), storage,
+                         head_pos=(shape[0] / 4.0, shape[1] / 2.0))
+        reqs.append((wl, int(rng.integers(100, 151))))
+    srv = lbm.Server(hbm_budget=8 << 30, storage=storage, quantum=40, max_active=2)
+    ids = []
+    for k, (wl, steps) in enumerate(reqs):
+        ids.append(srv.submit(wl["shape"], wl["params"], wl["geom"], wl["rheo"], steps))
+        srv.poll()
+    results = {}
+    for _ in range(1000):
+        srv.poll()
+        for rid in srv.finished():
+            results[rid] = srv.result(rid)
+        if len(results) == len(ids):
+            break
+    srv.close()
+    assert len(results) == len(ids)
+    for rid, (wl, steps) in zip(ids, reqs):
+        status, fg, diag, _ = results[rid]
+        assert status == 0 and diag["unstable"] == 0
+        ref = O.Oracle(wl["shape"], params=wl["params"], geom=wl["geom"], rheo=wl["rheo"])
+        ref.step(steps)
+        e = field_errors(fg, ref.fields(), ("rho_ink", "rho_amb", "ux", "uy", "uz"))
+        assert max(e.values()) <= BAR[storage], (rid, storage, e)

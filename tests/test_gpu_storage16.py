@@ -1,18 +1,19 @@
 """16-bit deviation storage (FP16 and BF16 populations, FP32 arithmetic, FP64
 reductions) against the FP64 oracle on the same seeded inputs.
 
-Bars. A stored population is rounded to 2^-11 (FP16) or 2^-8 (BF16) of its
-magnitude each step. The stored values are deviations from a local rest state
-(total deviation d_i; ink population minus c w_i rho_ref), of size up to
-~0.1 w_i in the print flow (the linear velocity term 3 w_i c_i.u and the
-recolouring term at the interface), so a step adds errors of ~1e-5 (FP16) and
-~1e-4 (BF16) to each population. They accumulate in the conserved moments and,
+Bar: the stated 1e-3 (max error over the field's scale) on every macroscopic
+field. A stored population is rounded to 2^-11 (FP16) or 2^-8 (BF16) of its
+magnitude each step; the stored values are deviations from a local rest state,
+of size up to ~0.1 w_i in the print flow, so a step adds ~1e-5 (FP16) or
+~1e-4 (BF16) to each population, accumulating in the conserved moments and,
 through the velocity, in the interface position. Measured on the 64x32x32
-print run after 200 steps: FP16 <= 4.2e-4 on the hydrodynamic fields, BF16
-<= 1.3e-2 (the largest on uz, the extrusion direction), BF16/FP16 ~ 2^3 as the
-rounding units predict. The bars below are those levels with a margin of
-about 2.5; nu (a difference of O(1) moments, see the FP32 parity tests) and
-rho^N (twice the colour-fraction error) have their own bars.
+print run after 200 steps: FP16 meets the bar on the densities, velocity and
+pressure (<= 4e-4) but not on the local viscosity nu (~1.8e-3: nu is read
+from the non-equilibrium stress, 10^-2..10^-3 of the stored deviations, so it
+amplifies their rounding); BF16 misses it on every field (1e-3 to 1e-2).
+Those cases are kept at the stated bar and marked as expected failures
+(strict: a case that starts to pass fails the run, so the record is kept
+current).
 """
 import os
 
@@ -27,8 +28,10 @@ from test_gpu_parity import _lbm, f32_exact, field_errors
 pytestmark = pytest.mark.gpu
 
 HYDRO = ("rho_ink", "rho_amb", "ux", "uy", "uz", "p")
-TOL16 = {"f16dev": 1e-3, "bf16dev": 3e-2}
-NU16 = {"f16dev": 6e-3, "bf16dev": 6e-2}
+DERIVED = ("nu", "rhoN")
+TOL16 = 1e-3
+BF16_FAILS = pytest.mark.xfail(strict=True, reason="BF16 deviations miss the 1e-3 bar (measured 1e-3..1e-2 at 200 "
+                                                  "steps, 8 significant bits)")
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "print_128x64x64_10k.npz")
 
 
@@ -38,15 +41,14 @@ def small_print_200():
     shape = wl["shape"]
     rY, rB = I.nozzle_fill(shape, wl["geom"])
     rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=0))
-    ref = O.Oracle(shape, params=wl["params"], geom=wl["geom"], rheo=wl["rheo"])
+    # FP32 arithmetic: the oracle takes FP32's rounding floor for Eq. 16
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f32"), geom=wl["geom"], rheo=wl["rheo"])
     ref.set_fields(rY, rB)
     ref.step(200)
     return wl, (rY, rB), ref.fields(), ref.diag()
 
 
-@pytest.mark.parametrize("path", ["plain", "fused"])
-@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
-def test_small_print_200_steps(small_print_200, storage, path):
+def _run200(small_print_200, storage, path):
     lbm = _lbm()
     wl, init, fo, do = small_print_200
     lat = lbm.Lattice(wl["shape"], dict(wl["params"], storage=storage), wl["geom"], wl["rheo"], path=path)
@@ -55,16 +57,40 @@ def test_small_print_200_steps(small_print_200, storage, path):
     fg = lat.fields()
     lat.close()
     assert fg["diag"]["unstable"] == 0
-    e = field_errors(fg, fo)
-    bad = {k: v for k, v in e.items() if k in HYDRO and not v <= TOL16[storage]}
-    assert not bad, "%s %s: %s" % (storage, path, bad)
-    assert e["nu"] <= NU16[storage], e
-    assert e["rhoN"] <= 2 * TOL16[storage], e
     assert np.array_equal(np.asarray(fg["solid"]) != 0, np.asarray(fo["solid"]) != 0)
-    # total ink mass (inflow included) to the storage's rounding level
+    return fg, fo, do
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("storage", ["f16dev", pytest.param("bf16dev", marks=BF16_FAILS)])
+def test_small_print_200_steps_hydrodynamic_fields(small_print_200, storage, path):
+    """Densities, velocity and pressure after 200 steps at 1e-3; the total
+    masses to the storage's rounding level."""
+    fg, fo, do = _run200(small_print_200, storage, path)
+    e = field_errors(fg, fo, HYDRO)
+    bad = {k: v for k, v in e.items() if not v <= TOL16}
+    assert not bad, "%s %s: %s" % (storage, path, bad)
     mg, mo = fg["diag"]["mass"], do["mass"]
-    assert abs(mg[0] / mo[0] - 1) <= 0.1 * TOL16[storage]
-    assert abs(mg[1] / mo[1] - 1) <= 0.01 * TOL16[storage]
+    assert abs(mg[0] / mo[0] - 1) <= 0.1 * TOL16
+    assert abs(mg[1] / mo[1] - 1) <= 0.01 * TOL16
+
+
+@pytest.mark.xfail(strict=True, reason="nu from 16-bit stored deviations misses 1e-3 (FP16 ~1.8e-3, BF16 ~1.5e-2 "
+                                       "at 200 steps)")
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_small_print_200_steps_viscosity(small_print_200, storage, path):
+    fg, fo, _ = _run200(small_print_200, storage, path)
+    e = field_errors(fg, fo, DERIVED)
+    assert e["nu"] <= TOL16, (storage, path, e)
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+@pytest.mark.parametrize("storage", ["f16dev", pytest.param("bf16dev", marks=BF16_FAILS)])
+def test_small_print_200_steps_phase_field(small_print_200, storage, path):
+    fg, fo, _ = _run200(small_print_200, storage, path)
+    e = field_errors(fg, fo, DERIVED)
+    assert e["rhoN"] <= TOL16, (storage, path, e)
 
 
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
@@ -93,7 +119,7 @@ def test_fp16_ragged_lattice_both_paths_agree_with_oracle():
     wl = I.print_run(shape, 4.0, 10, 0.01, 0.02, 0.6, "f16dev", head_pos=(12.0, 13.0))
     rY, rB = I.nozzle_fill(shape, wl["geom"])
     rY, rB = f32_exact(rY, I.perturbed_ambient(shape, rB, seed=3))
-    ref = O.Oracle(shape, params=dict(wl["params"], storage="f64"), geom=wl["geom"], rheo=wl["rheo"])
+    ref = O.Oracle(shape, params=dict(wl["params"], storage="f32"), geom=wl["geom"], rheo=wl["rheo"])
     ref.set_fields(rY, rB)
     ref.step(60)
     fo = ref.fields()
@@ -103,8 +129,8 @@ def test_fp16_ragged_lattice_both_paths_agree_with_oracle():
         lat.step(60)
         fg = lat.fields()
         lat.close()
-        e = field_errors(fg, fo, HYDRO)
-        assert max(e.values()) <= TOL16["f16dev"], (path, e)
+        e = field_errors(fg, fo, HYDRO + ("rhoN",))
+        assert max(e.values()) <= TOL16, (path, e)
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden file not generated")
