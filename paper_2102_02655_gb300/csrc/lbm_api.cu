@@ -546,12 +546,13 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->esize = cfg->storage == LBM_F64 ? 8 : 4;
     h->psize = cfg->storage == LBM_F64 ? 8 : (cfg->storage == LBM_F32 ? 4 : 2);
     {
-        // z-planes per CTA of the fused kernel: 152 x 12 CTAs in all, four
-        // waves of three CTAs per SM (16 and 24 planes measure the same on the
-        // 512x128x128 lattice), at least 4 planes so the two-plane prologue
-        // stays amortised
-        const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + 7) / 8);
-        long long chunks = (152LL * 12 + tiles - 1) / tiles;
+        // z-planes per CTA of the fused kernel: about four waves of CTAs
+        // (152 SMs), at least 4 planes so the two-plane prologue stays
+        // amortised
+        const bool fp64 = cfg->storage == LBM_F64;
+        const int th = fused_tile_rows(fp64);
+        const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + th - 1) / th);
+        long long chunks = (152LL * 4 * fused_ctas_per_sm(fp64) + tiles - 1) / tiles;
         chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));
         h->zchunk = std::max(4, (int)((cfg->nz + chunks - 1) / chunks));
         if (const char* e = getenv("CGLBM_ZCHUNK")) h->zchunk = std::max(1, atoi(e));

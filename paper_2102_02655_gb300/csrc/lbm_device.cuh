@@ -576,11 +576,21 @@ __device__ __forceinline__ real tau_zero_shear(const StepArgs<real>& p) {
 
 // Root of g tau_Y(g) = S / (rho_Y c_s^2) (Eq. 24-25) by Newton's method kept
 // inside the bracket [s / tau_max, s / tau_min] (bisection when a step leaves
-// it); stops when the relative step is below tol. Returns the clamped tau_Y.
+// it). Returns the clamped tau_Y.
+//
+// The root serves the mixture's relaxation time (Eq. 17), in which the ink's
+// viscosity enters with at most the weight w = (c_Y/nu_min) / (c_Y/nu_min +
+// c_B/nu_B) (nu_min: the viscosity at tau_min). A relative error e in tau_Y
+// moves the mixture's tau by at most about w e, so the iteration stops when
+// its relative step is below tol / w (tol when w = 1, at most 1e-2), and where
+// w <= tol the ink's viscosity cannot move tau by tol at all and its
+// zero-shear value is taken. Either way the mixture's tau is within tol
+// (relative) of the one the exact root gives.
 template <typename real>
-__device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, real rhoY, real rho) {
+__device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, real rhoY, real rho, real wmax) {
     if (p.law == kLawNewtonian) return clampr(real(0.5) + real(3) * p.nu0, p.tau_min, p.tau_max);
-    if (!(rhoY > real(1e-12) * rho) || !(S > real(0))) return tau_zero_shear(p);
+    if (!(rhoY > real(1e-12) * rho) || !(S > real(0)) || !(wmax > p.tol)) return tau_zero_shear(p);
+    const real tol = fmin(p.tol / wmax, real(1e-2));
     const real s = real(3) * S / rhoY;
     real lo = s / p.tau_max, hi = s / p.tau_min;
     real t, dt;
@@ -588,7 +598,18 @@ __device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, r
     if (t >= p.tau_max) return p.tau_max;  // root on the tau_max branch
     tau_law(p, hi, &t, &dt);
     if (t <= p.tau_min) return p.tau_min;  // root on the tau_min branch
-    real g = lo;
+    // start near the root: for the power law, the root of its larger term
+    // alone (g/2 = s or 3K g^n = s; an upper bound of the root, since both
+    // terms are positive); for the Cross law, one fixed-point step from the
+    // zero-shear relaxation time
+    real g;
+    if (p.law == kLawPower) {
+        g = fmin(real(2) * s, rpow(s * qdiv(real(1), real(3) * p.K), qdiv(real(1), p.n_exp)));
+    } else {
+        tau_law(p, s / tau_zero_shear(p), &t, &dt);
+        g = s / clampr(t, p.tau_min, p.tau_max);
+    }
+    g = clampr(g, lo, hi);
     for (int it = 0; it < p.max_iter; ++it) {
         tau_law(p, g, &t, &dt);
         if (t > p.tau_max) { t = p.tau_max; dt = real(0); }
@@ -599,7 +620,7 @@ __device__ __forceinline__ real solve_tau_ink(const StepArgs<real>& p, real S, r
         if (!(gn > lo && gn < hi)) gn = real(0.5) * (lo + hi);
         const real step = gn - g;
         g = gn;
-        if (fabs(step) <= p.tol * g) break;
+        if (fabs(step) <= tol * g) break;
     }
     tau_law(p, g, &t, &dt);
     return clampr(t, p.tau_min, p.tau_max);
@@ -685,26 +706,33 @@ __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2]
     real a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
+        rY += f[0][i];
+        sd += f[1][i];
+    }
+    // first and second moments over pairs of opposite directions (2q-1, 2q):
+    // the pair's sum carries the second moments, its difference the momentum
+#pragma unroll
+    for (int q = 0; q < (Q - 1) / 2; ++q) {
+        const int i = 2 * q + 1;
         const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-        const real fy = f[0][i], fd = f[1][i];
-        rY += fy;
-        sd += fd;
-        if (cx) mx += cx > 0 ? fd : -fd;
-        if (cy) my += cy > 0 ? fd : -fd;
-        if (cz) mz += cz > 0 ? fd : -fd;
-        if (cx) b[0] += fd;
-        if (cy) b[1] += fd;
-        if (cz) b[2] += fd;
-        if (cx && cy) b[3] += (cx == cy) ? fd : -fd;
-        if (cx && cz) b[4] += (cx == cz) ? fd : -fd;
-        if (cy && cz) b[5] += (cy == cz) ? fd : -fd;
+        const real ds = f[1][i] + f[1][i + 1], dd = f[1][i] - f[1][i + 1];
+        if (cx) mx += cx > 0 ? dd : -dd;
+        if (cy) my += cy > 0 ? dd : -dd;
+        if (cz) mz += cz > 0 ? dd : -dd;
+        if (cx) b[0] += ds;
+        if (cy) b[1] += ds;
+        if (cz) b[2] += ds;
+        if (cx && cy) b[3] += (cx == cy) ? ds : -ds;
+        if (cx && cz) b[4] += (cx == cz) ? ds : -ds;
+        if (cy && cz) b[5] += (cy == cz) ? ds : -ds;
         if constexpr (!kSplit) {
-            if (cx) a[0] += fy;
-            if (cy) a[1] += fy;
-            if (cz) a[2] += fy;
-            if (cx && cy) a[3] += (cx == cy) ? fy : -fy;
-            if (cx && cz) a[4] += (cx == cz) ? fy : -fy;
-            if (cy && cz) a[5] += (cy == cz) ? fy : -fy;
+            const real ys = f[0][i] + f[0][i + 1];
+            if (cx) a[0] += ys;
+            if (cy) a[1] += ys;
+            if (cz) a[2] += ys;
+            if (cx && cy) a[3] += (cx == cy) ? ys : -ys;
+            if (cx && cz) a[4] += (cx == cz) ? ys : -ys;
+            if (cy && cz) a[5] += (cy == cz) ? ys : -ys;
         }
     }
     const real rho = p.rho_ref + sd;
@@ -728,11 +756,14 @@ __device__ __forceinline__ void moments(const StepArgs<real>& p, const real f[2]
     if constexpr (kSplit) {
         // ink stress by the split above: c Pi + H - h0 (I/3 + u u) + c kappa I
         const real c = rY * irho;
-        real h0 = 0, H[6] = {0, 0, 0, 0, 0, 0};
+        real h0 = rfma(-c, f[1][0], rfma(-c, p.wref[0], f[0][0])), H[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int q = 0; q < (Q - 1) / 2; ++q) {
+            const int i = 2 * q + 1;
             const int cx = VS::c(i, 0), cy = VS::c(i, 1), cz = VS::c(i, 2);
-            const real h = rfma(-c, f[1][i], rfma(-c, p.wref[i], f[0][i]));
+            // opposite directions share w_i, so wref too
+            const real h = rfma(-c, f[1][i], rfma(-c, p.wref[i], f[0][i])) +
+                           rfma(-c, f[1][i + 1], rfma(-c, p.wref[i], f[0][i + 1]));
             h0 += h;
             if (cx) H[0] += h;
             if (cy) H[1] += h;
@@ -842,7 +873,9 @@ __device__ __forceinline__ void collide_out(const StepArgs<real>& p, const Momen
     // by mass fraction (Eq. 17), clamp
     const real S = qsqrt(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
                          real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
-    const real tauY = solve_tau_ink(p, S, rY, rho);
+    // the ink's largest weight in Eq. 17 (its viscosity at least nu_min)
+    const real aYm = qdiv(cY0 * real(3), p.tau_min - real(0.5)), aBm = qdiv(cB0, p.nuB);
+    const real tauY = solve_tau_ink(p, S, rY, rho, qdiv(aYm, aYm + aBm));
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
     const real inv_nu = qdiv(cY0, nuY) + qdiv(cB0, p.nuB);
     const real tau = clampr(real(0.5) + qdiv(real(3), inv_nu), p.tau_min, p.tau_max);

@@ -219,21 +219,24 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
     *rB = (p.rho_ref + b) - a;
 }
 
-// The own sites' pulled populations wait in shared memory for their
-// collision (one plane later); each thread reads back only its own column.
 // One tile column (x0, y0) of planes [za, zb) of one lattice; shared memory
 // as laid out by fused_smem. Used by the single-lattice kernel (one column
 // per CTA) and by the persistent batched kernel (a list of columns per CTA).
-// The own sites wait for their collision as their 17 moments (see moments())
-// rather than their 38 populations: less than half the shared memory and
-// none of the populations' registers across the plane.
-template <typename real, typename S, bool kUnit, int TY_, int TX_ = 32>
+// The CTA has 32 x 8 threads; each owns R sites of the 32 x 8R tile, at rows
+// ty, ty + 8, ..., so that a thread carries R independent pulls and
+// collisions (instruction-level parallelism) and the halo ring is shared by
+// more sites. The own sites wait for their collision as their 17 moments
+// (see moments()) rather than their 38 populations: less than half the
+// shared memory and none of the populations' registers across the plane.
+template <typename real, typename S, bool kUnit, int R>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
-    using T = Tile<TY_, TX_>;
-    constexpr int TX = T::TX, TY = T::TY, NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
+    using T = Tile<8 * R, 32>;
+    constexpr int NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
+    constexpr int NTH = 256;                        // threads
     constexpr int NS = 17;                          // moments staged per site
+    static_assert(NRING <= NTH && SS - HS <= NTH, "one ring site per thread");
     real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][NS][NT]
     Colour<real, kUnit, HS> C{pops + 2 * NS * NT};  // [4 slots][NV][HS]
     // substrate prologue scratch [2][SS]: staging buffer 1, first written
@@ -254,54 +257,62 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             b[(11 + k) * NT] = M.PT[k];
         }
     };
-    (void)TX;
-    (void)TY;
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool in_xy = x < p.nx && y < p.ny;
-    const int gx = in_xy ? x : wrapn(x, p.nx), gy = in_xy ? y : wrapn(y, p.ny);
-    const int hidx = (ty + 1) * HX + (tx + 1);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    int xs[R], ys[R], gxs[R], gys[R], hidx[R];
+    bool in_xy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        xs[r] = x0 + tx;
+        ys[r] = y0 + ty + 8 * r;
+        in_xy[r] = xs[r] < p.nx && ys[r] < p.ny;
+        gxs[r] = in_xy[r] ? xs[r] : wrapn(xs[r], p.nx);
+        gys[r] = in_xy[r] ? ys[r] : wrapn(ys[r], p.ny);
+        hidx[r] = (ty + 8 * r + 1) * HX + (tx + 1);
+    }
     double bc[2] = {0.0, 0.0};
 
-    // Densities after streaming on plane zz for the tile and its halo ring
-    // (items 0 and 1), and with outer > 0 also the second ring (item 2, the
-    // substrate prologue). Item 0 is the thread's own site: its populations go
-    // to buffer zz & 1 and its boundary-link mass is booked once, for this
+    // Densities after streaming on plane zz for the tile (items 0 .. R-1, the
+    // own sites) and its halo ring (item R), and with outer also the second
+    // ring (item R + 1, the substrate prologue). The own sites' moments go to
+    // buffer zz & 1 and their boundary-link mass is booked once, for this
     // chunk's planes. One pull body serves every item.
     auto load_plane = [&](int zz, bool keep, bool outer) {
-        const int nitems = outer ? 3 : 2;
+        const int nitems = R + (outer ? 2 : 1);
         for (int it = 0; it < nitems; ++it) {
             int hx, hy;  // coordinates in the tile grown by two rings
-            if (it == 0) {
+            int r = -1;
+            if (it < R) {
+                r = it;
                 hx = tx + 2;
-                hy = ty + 2;
-            } else if (it == 1) {
+                hy = ty + 8 * r + 2;
+            } else if (it == R) {
                 if (tid >= NRING) continue;
                 ring_coord<HX, HY>(tid, &hx, &hy);
                 hx += 1;
                 hy += 1;
             } else {
                 if (tid >= SS - HS) continue;
-                // the 92 sites of the second ring
+                // the sites of the second ring
                 const int j = tid;
                 if (j < SX) { hx = j; hy = 0; }
                 else if (j < 2 * SX) { hx = j - SX; hy = SY - 1; }
                 else { const int k = j - 2 * SX; hy = 1 + (k >> 1); hx = (k & 1) ? SX - 1 : 0; }
             }
             const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
-            const bool own = it == 0;
-            real* dst = own && keep ? pops + (zz & 1) * NS * NT + tid : nullptr;
+            const bool own = r >= 0;
+            real* dst = own && keep ? pops + (zz & 1) * NS * NT + tid + NTH * r : nullptr;
             real rY, rB;
             if (zz == p.nz - 1) {
-                const bool led = own && keep && in_xy && zz < zb && !in_box(p, x, y, zz);
+                const bool led = own && keep && in_xy[r < 0 ? 0 : r] && zz < zb &&
+                                 !in_box(p, xs[r < 0 ? 0 : r], ys[r < 0 ? 0 : r], zz);
                 real ft[2][19];
-                const TopPull<real> r = pull_top<S>(p, px, py, ft, led);
+                const TopPull<real> res = pull_top<S>(p, px, py, ft, led);
                 if (dst) stage(dst, ft);
-                rY = r.rY;
-                rB = r.rB;
-                bc[0] += r.b0;
-                bc[1] += r.b1;
+                rY = res.rY;
+                rB = res.rB;
+                bc[0] += res.b0;
+                bc[1] += res.b1;
             } else {
                 real f[2][19];
                 pull_interior<S>(p, px, py, zz, f);
@@ -312,13 +323,13 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                 sub[hy * SX + hx] = rY;
                 sub[SS + hy * SX + hx] = rB;
             }
-            if (it < 2) C.put(p, slot_of(zz), (hy - 1) * HX + (hx - 1), rY, rB);
+            if (it <= R) C.put(p, slot_of(zz), (hy - 1) * HX + (hx - 1), rY, rB);
         }
     };
 
-    // Plane zz below the top (1 <= zz <= nz - 2) for the own site (kept in
-    // buffer zz & 1) and the halo site: both pulls are issued before either
-    // is consumed, so the halo threads wait for one memory round trip, not two.
+    // Plane zz below the top (1 <= zz <= nz - 2): the own sites' pulls are
+    // issued together (R independent memory round trips in flight), then the
+    // halo site's.
     const bool has_halo = tid < NRING;
     int rx = 0, ry = 0;
     if (has_halo) ring_coord<HX, HY>(tid, &rx, &ry);
@@ -326,14 +337,16 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     const int hj = ry * HX + rx;
     auto load_interior = [&](int zz) {
         real rY, rB;
-        // one pull at a time: the register budget of three CTAs per SM holds
-        // one site's 38 values, not two
         {
-            real f[2][19];
-            pull_interior<S>(p, gx, gy, zz, f);
-            stage(pops + (zz & 1) * NS * NT + tid, f);
-            density(f, p, &rY, &rB);
-            C.put(p, slot_of(zz), hidx, rY, rB);
+            real f[R][2][19];
+#pragma unroll
+            for (int r = 0; r < R; ++r) pull_interior<S>(p, gxs[r], gys[r], zz, f[r]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                stage(pops + (zz & 1) * NS * NT + tid + NTH * r, f[r]);
+                density(f[r], p, &rY, &rB);
+                C.put(p, slot_of(zz), hidx[r], rY, rB);
+            }
         }
         if (has_halo) {
             real h[2][19];
@@ -349,7 +362,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         // the fictitious-density rule (Eq. 18) from its five fluid neighbours
         load_plane(0, true, true);
         __syncthreads();
-        for (int j = tid; j < HS; j += NT) {
+        for (int j = tid; j < HS; j += NTH) {
             const int hx = j % HX, hy = j / HX;
             const int c = (hy + 1) * SX + (hx + 1);
             real n0 = 0, n1 = 0, den = 0;
@@ -372,22 +385,26 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
 
     double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
     int bad = 0;
+    const int N = (int)p.N;
     for (int z = za; z < zb; ++z) {
-        // plane z + 1 goes to colour slot (z + 1) mod 4 and population buffer
+        // plane z + 1 goes to colour slot (z + 1) mod 4 and moment buffer
         // (z + 1) & 1: no collision still running (plane z - 1, other threads)
         // reads that slot, and the buffer's previous plane was read by this
         // thread only
         if (z + 1 < p.nz - 1) load_interior(z + 1);
         else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
         __syncthreads();
-        if (in_xy && !in_box(p, x, y, z)) {
-            // open top: zero normal gradient, the ghost plane above is the top plane
-            const int sup = z + 1 < p.nz ? slot_of(z + 1) : slot_of(z);
-            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx};
+        // open top: zero normal gradient, the ghost plane above is the top plane
+        const int sup = z + 1 < p.nz ? slot_of(z + 1) : slot_of(z);
+        // the own sites that belong to this kernel (not outside the lattice,
+        // not in the nozzle box, whose sites pull from wall nodes here)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!(in_xy[r] && !in_box(p, xs[r], ys[r], z))) continue;
+            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx[r]};
             SiteOut<real> so;
-            const int s = z * (int)p.plane + y * p.nx + x;
-            const int N = (int)p.N;
-            const real* b = pops + (z & 1) * NS * NT + tid;
+            const int s = z * (int)p.plane + gys[r] * p.nx + gxs[r];
+            const real* b = pops + (z & 1) * NS * NT + tid + NTH * r;
             Moments<real> M;
             M.rY = b[0];
             M.sd = b[NT];
@@ -404,7 +421,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                                             });
             ref_put<S>(p, s, so.cY);
             if (z >= p.nz - 2)
-                for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, x, y, z)] = so.u[a];
+                for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, xs[r], ys[r], z)] = so.u[a];
             if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
             if (p.write_fields) {
                 real* F = p.fields;
@@ -438,24 +455,29 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int TY_, int TX_ = 32>
+template <typename real, bool kUnit, int R>
 constexpr size_t fused_smem() {
-    using T = Tile<TY_, TX_>;
+    using T = Tile<8 * R, 32>;
     return sizeof(real) * (2 * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
 }
 
-// Configuration of the bulk kernel: 32 x 8 tiles, three CTAs per SM in FP32
-// arithmetic (80 registers), one in FP64.
+// Configuration of the single-lattice bulk kernel: one site per thread
+// (32 x 8 tiles), three CTAs of 256 threads per SM in FP32 arithmetic (80
+// registers), one in FP64. (Two sites per thread, 32 x 16 tiles at two CTAs
+// per SM, measured 20% slower on the print lattice.)
+template <typename real>
+constexpr int fused_rows() { return 1; }
 template <typename real>
 constexpr int fused_minb() { return sizeof(real) == 8 ? 1 : 3; }
-constexpr int kTileH = 8;
+constexpr int kTileH = 8;  // rows of the batched kernel's tiles (one site per thread)
 
 template <typename real, typename S, bool kUnit>
-__global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>()) k_fused(StepArgs<real> p, int zchunk) {
+__global__ void __launch_bounds__(256, fused_minb<real>()) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int R = fused_rows<real>();
     const int n = z_chunks(p.nz, zchunk);
-    fused_column<real, S, kUnit, kTileH>(p, smraw, blockIdx.x * 32, blockIdx.y * kTileH,
-                                         z_chunk_begin(p.nz, n, blockIdx.z), z_chunk_begin(p.nz, n, blockIdx.z + 1));
+    fused_column<real, S, kUnit, R>(p, smraw, blockIdx.x * 32, blockIdx.y * 8 * R, z_chunk_begin(p.nz, n, blockIdx.z),
+                                    z_chunk_begin(p.nz, n, blockIdx.z + 1));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -463,8 +485,13 @@ __global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>()) k_fused(
 // zero at launch), so CTAs that become resident late, behind other kernels,
 // simply take fewer columns. Each lattice's step arguments are copied to
 // shared memory when a CTA's column changes lattice.
+// the batched kernel keeps one site per thread at three CTAs per SM (FP32),
+// leaving room on the SMs for the batched box kernels beside it
+template <typename real>
+constexpr int batch_minb() { return sizeof(real) == 8 ? 1 : 3; }
+
 template <typename real, typename S, bool kUnit>
-__global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>())
+__global__ void __launch_bounds__(Tile<kTileH>::NT, batch_minb<real>())
     k_fused_batch(const StepArgs<real>* __restrict__ args, const int4* __restrict__ items, int n_items,
                   int* __restrict__ queue) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -487,7 +514,7 @@ __global__ void __launch_bounds__(Tile<kTileH>::NT, fused_minb<real>())
             last = it.x;
             __syncthreads();
         }
-        fused_column<real, S, kUnit, kTileH>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
+        fused_column<real, S, kUnit, 1>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
     }
 }
 
@@ -504,12 +531,13 @@ void set_smem_once(K kernel, size_t smem, unsigned* configured) {
 
 template <typename real, typename S, bool kUnit>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr size_t smem = fused_smem<real, kUnit, kTileH>();
-    static_assert(smem <= 227 * 1024, "shared memory of one CTA");
+    constexpr int R = fused_rows<real>();
+    constexpr size_t smem = fused_smem<real, kUnit, R>();
+    static_assert(smem * fused_minb<real>() <= 227 * 1024, "CTAs per SM");
     static unsigned configured = 0;
     set_smem_once(k_fused<real, S, kUnit>, smem, &configured);
-    dim3 block(32, kTileH);
-    dim3 grid((p.nx + 31) / 32, (p.ny + kTileH - 1) / kTileH, z_chunks(p.nz, zchunk));
+    dim3 block(32, 8);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 8 * R - 1) / (8 * R), z_chunks(p.nz, zchunk));
     k_fused<real, S, kUnit><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
@@ -517,7 +545,7 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
 template <typename real, typename S, bool kUnit>
 int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
                      cudaStream_t st, int* occupancy) {
-    constexpr size_t smem = fused_smem<real, kUnit, kTileH>();
+    constexpr size_t smem = fused_smem<real, kUnit, 1>();
     static unsigned configured = 0;
     set_smem_once(k_fused_batch<real, S, kUnit>, smem, &configured);
     if (occupancy) {

@@ -44,8 +44,12 @@ int launch_fused(const StepArgs<real>& p, int zchunk, cudaStream_t st);
 template <typename real, typename S>
 int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid, int unit,
                        cudaStream_t st, int* occupancy);
-// tile height (sites in y) of the fused kernels' 32-wide column tiles
+// tile height (sites in y) of the batched fused kernel's 32-wide column tiles
 constexpr int kFusedTileH = 8;
+// tile height and resident CTAs per SM of the single-lattice fused kernel:
+// 32 x 8 tiles, three CTAs per SM in FP32 arithmetic, one in FP64
+inline int fused_tile_rows(bool) { return 8; }
+inline int fused_ctas_per_sm(bool fp64) { return fp64 ? 1 : 3; }
 
 // Batched phase-by-phase step of the nozzle boxes of many lattices: one
 // launch per phase over all lattices (blockIdx.z), each lattice's StepArgs
