@@ -292,14 +292,18 @@ def run_ours(args):
         lat.close()
         lat = None
         torch.cuda.empty_cache()
-        sweep = run_sweep(args, local)
+        with Clocks(local) as clk_w:
+            sweep = run_sweep(args, local)
+        sweep["clocks"] = clk_w.summary()
     serving = None
     if rank == 0 and not args.no_serve:
         if lat is not None:
             lat.close()
             lat = None
         torch.cuda.empty_cache()
-        serving = run_serving(args, local)
+        with Clocks(local) as clk_s:
+            serving = run_serving(args, local)
+        serving["clocks"] = clk_s.summary()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as O

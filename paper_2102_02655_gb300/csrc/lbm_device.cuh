@@ -193,21 +193,37 @@ struct Stored<__nv_bfloat16> {
 // positive quantity trailing off to zero loses mass. The scaling is exact.
 constexpr float kF16Scale = 8192.0f, kF16Unscale = 1.0f / 8192.0f;
 
-template <typename S, typename real, typename Idx>
-__device__ __forceinline__ real s_get(const void* b, Idx k) {
-    if constexpr (std::is_same<S, __half>::value)
-        return __half2float(static_cast<const __half*>(b)[k]) * kF16Unscale;
-    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
-        return __bfloat162float(static_cast<const __nv_bfloat16*>(b)[k]);
-    else return static_cast<const real*>(b)[k];
+// The two slots of element k = i N + s (direction i, site s of N) as
+// stored: FP64 and FP32 keep the slots in two arrays Q N elements apart
+// (slot-major, [2][Q][N]); the 16-bit types keep them side by side, one
+// 32-bit word per direction and site ([Q][N][2]), so that a pull or a store
+// moves both slots in one access and converts them in one instruction.
+template <class VS, typename S, typename real, typename Idx>
+__device__ __forceinline__ void slots_get(const void* b, Idx k, Idx N, real* a, real* d) {
+    if constexpr (std::is_same<S, __half>::value) {
+        const float2 v = __half22float2(static_cast<const __half2*>(b)[k]);
+        *a = v.x * kF16Unscale;
+        *d = v.y * kF16Unscale;
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        const float2 v = __bfloat1622float2(static_cast<const __nv_bfloat162*>(b)[k]);
+        *a = v.x;
+        *d = v.y;
+    } else {
+        *a = static_cast<const real*>(b)[k];
+        *d = static_cast<const real*>(b)[k + (Idx)VS::Q * N];
+    }
 }
 
-template <typename S, typename real, typename Idx>
-__device__ __forceinline__ void s_put(void* b, Idx k, real v) {
-    if constexpr (std::is_same<S, __half>::value) static_cast<__half*>(b)[k] = __float2half_rn(v * kF16Scale);
-    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
-        static_cast<__nv_bfloat16*>(b)[k] = __float2bfloat16_rn(v);
-    else static_cast<real*>(b)[k] = v;
+template <class VS, typename S, typename real, typename Idx>
+__device__ __forceinline__ void slots_put(void* b, Idx k, Idx N, real a, real d) {
+    if constexpr (std::is_same<S, __half>::value) {
+        static_cast<__half2*>(b)[k] = __floats2half2_rn(a * kF16Scale, d * kF16Scale);
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        static_cast<__nv_bfloat162*>(b)[k] = __floats2bfloat162_rn(a, d);
+    } else {
+        static_cast<real*>(b)[k] = a;
+        static_cast<real*>(b)[k + (Idx)VS::Q * N] = d;
+    }
 }
 
 // Both slots of direction i written at site s (of N) into buffer b with
@@ -216,8 +232,7 @@ __device__ __forceinline__ void s_put(void* b, Idx k, real v) {
 template <class VS, typename S, typename real, typename Idx>
 __device__ __forceinline__ void pop_get(const StepArgs<real>& p, const void* b, const real* ref, int i, Idx s, Idx N,
                                         real* fY, real* fD) {
-    *fY = s_get<S, real>(b, (Idx)i * N + s);
-    *fD = s_get<S, real>(b, (Idx)(VS::Q + i) * N + s);
+    slots_get<VS, S>(b, (Idx)i * N + s, N, fY, fD);
     if constexpr (Stored<S>::kDev) *fY += (real)VS::w(i) * p.rho_ref * ref[s];
 }
 
@@ -226,8 +241,7 @@ __device__ __forceinline__ void pop_get(const StepArgs<real>& p, const void* b, 
 template <class VS, typename S, typename real, typename Idx>
 __device__ __forceinline__ void pop_put(const StepArgs<real>& p, int i, Idx s, Idx N, real fY, real fD, real c) {
     if constexpr (Stored<S>::kDev) fY -= (real)VS::w(i) * p.rho_ref * c;
-    s_put<S, real>(p.fout, (Idx)i * N + s, fY);
-    s_put<S, real>(p.fout, (Idx)(VS::Q + i) * N + s, fD);
+    slots_put<VS, S>(p.fout, (Idx)i * N + s, N, fY, fD);
 }
 
 template <typename S, typename real, typename Idx>
@@ -574,6 +588,15 @@ __device__ __forceinline__ real tau_zero_shear(const StepArgs<real>& p) {
     return clampr(real(0.5) + real(3) * p.nu0, p.tau_min, p.tau_max);
 }
 
+// The ink's largest weight in the mixture's relaxation time (Eq. 17), with
+// its viscosity at least nu_min (that at tau_min): (c_Y/nu_min) / (c_Y/nu_min +
+// c_B/nu_B). cY, cB: the site's colour fractions.
+template <typename real>
+__device__ __forceinline__ real ink_weight(const StepArgs<real>& p, real cY, real cB) {
+    const real aYm = qdiv(cY * real(3), p.tau_min - real(0.5)), aBm = qdiv(cB, p.nuB);
+    return qdiv(aYm, aYm + aBm);
+}
+
 // Root of g tau_Y(g) = S / (rho_Y c_s^2) (Eq. 24-25) by Newton's method kept
 // inside the bracket [s / tau_max, s / tau_min] (bisection when a step leaves
 // it). Returns the clamped tau_Y.
@@ -873,9 +896,7 @@ __device__ __forceinline__ void collide_out(const StepArgs<real>& p, const Momen
     // by mass fraction (Eq. 17), clamp
     const real S = qsqrt(PY[0] * PY[0] + PY[1] * PY[1] + PY[2] * PY[2] +
                          real(2) * (PY[3] * PY[3] + PY[4] * PY[4] + PY[5] * PY[5]));
-    // the ink's largest weight in Eq. 17 (its viscosity at least nu_min)
-    const real aYm = qdiv(cY0 * real(3), p.tau_min - real(0.5)), aBm = qdiv(cB0, p.nuB);
-    const real tauY = solve_tau_ink(p, S, rY, rho, qdiv(aYm, aYm + aBm));
+    const real tauY = solve_tau_ink(p, S, rY, rho, ink_weight(p, cY0, cB0));
     const real nuY = (tauY - real(0.5)) * real(1.0 / 3.0);
     const real inv_nu = qdiv(cY0, nuY) + qdiv(cB0, p.nuB);
     const real tau = clampr(real(0.5) + qdiv(real(3), inv_nu), p.tau_min, p.tau_max);

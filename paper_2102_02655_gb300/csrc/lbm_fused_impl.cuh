@@ -43,8 +43,14 @@ __device__ __forceinline__ int slot_of(int z) { return (z + 4) & 3; }  // z >= -
 // substrate, where the resting half-way wall bounces the population back
 // (the pull then reads the opposite direction at the site itself). Branch-free:
 // the substrate case is an address select on the upward directions only.
-template <typename S, typename real>
-__device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19]) {
+//
+// With 16-bit storage the pull adds back c(x - c_i) w_i rho_ref (see Stored)
+// from the source sites' ink fractions: read from p.ref_in, or, when rs is
+// given, from shared memory: rs[k] holds plane zz - 1 + k of the tile's
+// ink fractions on a box of row width W, and the site is entry rj of it.
+template <typename S, typename real, int W = 0>
+__device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, int gy, int zz, real f[2][19],
+                                              const real* const* rs = nullptr, int rj = 0) {
     using VS = D3Q19;
     const int nx = p.nx, ny = p.ny, pl = (int)p.plane, N = (int)p.N;
     const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
@@ -63,9 +69,13 @@ __device__ __forceinline__ void pull_interior(const StepArgs<real>& p, int gx, i
             idx = bottom ? opp(i) * N + s : idx;
             src = bottom ? s : src;
         }
-        f[0][i] = s_get<S, real>(p.fin, idx);
-        f[1][i] = s_get<S, real>(p.fin, idx + 19 * N);
-        if constexpr (Stored<S>::kDev) f[0][i] += (real)VS::w(i) * p.rho_ref * p.ref_in[src];
+        slots_get<VS, S>(p.fin, idx, N, &f[0][i], &f[1][i]);
+        if constexpr (Stored<S>::kDev) {
+            real c;
+            if constexpr (W > 0) c = rs[1 - cz][rj - cy * W - cx];
+            else c = p.ref_in[src];
+            f[0][i] += (real)VS::w(i) * p.rho_ref * c;
+        }
     }
 }
 
@@ -103,8 +113,7 @@ __device__ __forceinline__ TopPull<real> pull_top(const StepArgs<real>& p, int g
         const int sy = cy > 0 ? rm : (cy < 0 ? rp : r0);
         const int src = bnd ? s : zoff - cz * pl + sy + sx;
         const int a = (bnd ? opp(i) : i) * N + src;  // w_i = w_opp(i)
-        f[0][i] = s_get<S, real>(p.fin, a);
-        f[1][i] = s_get<S, real>(p.fin, a + 19 * N);
+        slots_get<VS, S>(p.fin, a, N, &f[0][i], &f[1][i]);
         if constexpr (Stored<S>::kDev) f[0][i] += (real)VS::w(i) * p.rho_ref * p.ref_in[src];
     }
     real u0[3];
@@ -153,15 +162,21 @@ __device__ __forceinline__ void warp_add(double* dst, double v) {
     if (lane == 0 && v != 0.0) atomicAdd(dst, v);
 }
 
+// column (x, y) inside the nozzle box's columns (any plane)
 template <typename real>
-__device__ __forceinline__ bool in_box(const StepArgs<real>& p, int x, int y, int z) {
+__device__ __forceinline__ bool in_box_xy(const StepArgs<real>& p, int x, int y) {
     const Region& b = p.box;
-    if (b.wx == 0 || z < b.z0 || z >= b.z1) return false;
+    if (b.wx == 0) return false;
     int dx = x - b.x0;
     if (dx < 0) dx += p.nx;
     int dy = y - b.y0;
     if (dy < 0) dy += p.ny;
     return dx < b.wx && dy < b.wy;
+}
+
+template <typename real>
+__device__ __forceinline__ bool in_box(const StepArgs<real>& p, int x, int y, int z) {
+    return z >= p.box.z0 && z < p.box.z1 && in_box_xy(p, x, y);
 }
 
 template <typename real, bool kUnit, int HS>
@@ -239,14 +254,21 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     static_assert(NRING <= NTH && SS - HS <= NTH, "one ring site per thread");
     real* pops = reinterpret_cast<real*>(smraw);   // [2 buffers][NS][NT]
     Colour<real, kUnit, HS> C{pops + 2 * NS * NT};  // [4 slots][NV][HS]
+    // 16-bit storage: the ink fractions of the source sites, four planes of
+    // the tile grown by two rings ([4 slots][SS], plane q in slot q mod 4)
+    constexpr bool kRef = Stored<S>::kDev;
+    real* refs = C.col + 4 * Colour<real, kUnit, HS>::NV * HS;
     // substrate prologue scratch [2][SS]: staging buffer 1, first written
     // after the prologue's last read of it
     real* sub = pops + NS * NT;
     static_assert(NS * NT >= 2 * SS, "substrate scratch");
-    // a site waits for its collision as its 17 moments (see moments())
-    auto stage = [&](real* b, const real f[2][19]) {
+    // a site waits for its collision as its 17 moments (see moments()); its
+    // densities after streaming, for the colour plane, come with them
+    auto stage = [&](real* b, const real f[2][19], real* rY, real* rB) {
         Moments<real> M;
         moments<D3Q19>(p, f, &M);
+        *rY = M.rY;
+        *rB = (p.rho_ref + M.sd) - M.rY;
         b[0] = M.rY;
         b[NT] = M.sd;
 #pragma unroll
@@ -270,6 +292,10 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         gys[r] = in_xy[r] ? ys[r] : wrapn(ys[r], p.ny);
         hidx[r] = (ty + 8 * r + 1) * HX + (tx + 1);
     }
+    // the nozzle box's column test, once per column (its planes per plane)
+    bool box_xy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) box_xy[r] = in_box_xy(p, xs[r], ys[r]);
     double bc[2] = {0.0, 0.0};
 
     // Densities after streaming on plane zz for the tile (items 0 .. R-1, the
@@ -308,7 +334,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                                  !in_box(p, xs[r < 0 ? 0 : r], ys[r < 0 ? 0 : r], zz);
                 real ft[2][19];
                 const TopPull<real> res = pull_top<S>(p, px, py, ft, led);
-                if (dst) stage(dst, ft);
+                if (dst) stage(dst, ft, &rY, &rB);
                 rY = res.rY;
                 rB = res.rB;
                 bc[0] += res.b0;
@@ -316,8 +342,8 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
             } else {
                 real f[2][19];
                 pull_interior<S>(p, px, py, zz, f);
-                if (dst) stage(dst, f);
-                density(f, p, &rY, &rB);
+                if (dst) stage(dst, f, &rY, &rB);
+                else density(f, p, &rY, &rB);
             }
             if (outer) {
                 sub[hy * SX + hx] = rY;
@@ -335,26 +361,50 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (has_halo) ring_coord<HX, HY>(tid, &rx, &ry);
     const int hgx = wrapn(x0 - 1 + rx, p.nx), hgy = wrapn(y0 - 1 + ry, p.ny);
     const int hj = ry * HX + rx;
+    // ink fractions of plane q on the tile grown by two rings (16-bit storage)
+    auto load_ref = [&](int q) {
+        for (int j = tid; j < SS; j += NTH) {
+            const int gx = wrapn(x0 - 2 + j % SX, p.nx), gy = wrapn(y0 - 2 + j / SX, p.ny);
+            refs[(q & 3) * SS + j] = p.ref_in[(long long)q * p.plane + (long long)gy * p.nx + gx];
+        }
+    };
     auto load_interior = [&](int zz) {
         real rY, rB;
+        const real* rs[3] = {refs + ((zz - 1) & 3) * SS, refs + (zz & 3) * SS, refs + ((zz + 1) & 3) * SS};
         {
             real f[R][2][19];
 #pragma unroll
-            for (int r = 0; r < R; ++r) pull_interior<S>(p, gxs[r], gys[r], zz, f[r]);
+            for (int r = 0; r < R; ++r) {
+                if constexpr (kRef)
+                    pull_interior<S, real, SX>(p, gxs[r], gys[r], zz, f[r], rs, (ty + 8 * r + 2) * SX + tx + 2);
+                else
+                    pull_interior<S>(p, gxs[r], gys[r], zz, f[r]);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                stage(pops + (zz & 1) * NS * NT + tid + NTH * r, f[r]);
-                density(f[r], p, &rY, &rB);
+                stage(pops + (zz & 1) * NS * NT + tid + NTH * r, f[r], &rY, &rB);
                 C.put(p, slot_of(zz), hidx[r], rY, rB);
             }
         }
         if (has_halo) {
             real h[2][19];
-            pull_interior<S>(p, hgx, hgy, zz, h);
+            if constexpr (kRef)
+                pull_interior<S, real, SX>(p, hgx, hgy, zz, h, rs, (ry + 1) * SX + rx + 1);
+            else
+                pull_interior<S>(p, hgx, hgy, zz, h);
             density(h, p, &rY, &rB);
             C.put(p, slot_of(zz), hj, rY, rB);
         }
     };
+
+    // 16-bit storage: the pull of interior plane zz (1 <= zz <= nz - 2) reads
+    // the ink fractions of planes zz - 1 .. zz + 1 from shared memory. Planes
+    // za .. za + 2 are loaded here, and iteration z loads plane z + 3 into the
+    // slot of plane z - 1, whose last reader (the pull of plane z, one
+    // iteration earlier) is behind that iteration's barrier.
+    const int zref_end = min(zb + 1, p.nz - 1);  // last plane an interior pull reads
+    if constexpr (kRef)
+        for (int q = za; q <= min(za + 2, zref_end); ++q) load_ref(q);
 
     // prologue: planes za - 1 and za
     if (za == 0) {
@@ -381,6 +431,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     } else {
         load_plane(za - 1, false, false);
         load_plane(za, true, false);
+        if constexpr (kRef) __syncthreads();  // the ink fractions loaded above
     }
 
     double m0 = 0, m1 = 0, mx = 0, my = 0, mz = 0;
@@ -391,6 +442,8 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         // (z + 1) & 1: no collision still running (plane z - 1, other threads)
         // reads that slot, and the buffer's previous plane was read by this
         // thread only
+        if constexpr (kRef)
+            if (z + 3 <= zref_end) load_ref(z + 3);
         if (z + 1 < p.nz - 1) load_interior(z + 1);
         else if (z + 1 == p.nz - 1) load_plane(z + 1, true, false);
         __syncthreads();
@@ -400,7 +453,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         // not in the nozzle box, whose sites pull from wall nodes here)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (!(in_xy[r] && !in_box(p, xs[r], ys[r], z))) continue;
+            if (!in_xy[r] || (box_xy[r] && z >= p.box.z0 && z < p.box.z1)) continue;
             SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx[r]};
             SiteOut<real> so;
             const int s = z * (int)p.plane + gys[r] * p.nx + gxs[r];
@@ -455,10 +508,11 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, bool kUnit, int R>
+template <typename real, typename S, bool kUnit, int R>
 constexpr size_t fused_smem() {
     using T = Tile<8 * R, 32>;
-    return sizeof(real) * (2 * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS);
+    return sizeof(real) * (2 * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS +
+                           (Stored<S>::kDev ? 4 * T::SS : 0));
 }
 
 // Configuration of the single-lattice bulk kernel: one site per thread
@@ -532,7 +586,7 @@ void set_smem_once(K kernel, size_t smem, unsigned* configured) {
 template <typename real, typename S, bool kUnit>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
     constexpr int R = fused_rows<real>();
-    constexpr size_t smem = fused_smem<real, kUnit, R>();
+    constexpr size_t smem = fused_smem<real, S, kUnit, R>();
     static_assert(smem * fused_minb<real>() <= 227 * 1024, "CTAs per SM");
     static unsigned configured = 0;
     set_smem_once(k_fused<real, S, kUnit>, smem, &configured);
@@ -545,7 +599,7 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
 template <typename real, typename S, bool kUnit>
 int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
                      cudaStream_t st, int* occupancy) {
-    constexpr size_t smem = fused_smem<real, kUnit, 1>();
+    constexpr size_t smem = fused_smem<real, S, kUnit, 1>();
     static unsigned configured = 0;
     set_smem_once(k_fused_batch<real, S, kUnit>, smem, &configured);
     if (occupancy) {

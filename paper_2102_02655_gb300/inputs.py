@@ -111,3 +111,86 @@ def droplet(shape, center, radius, width=2.0, inside=1.0, outside=1.0):
     c = 0.5 * (1.0 - np.tanh((r - radius) / width))
     c = np.broadcast_to(c, (nz, ny, nx))
     return inside * c, outside * (1.0 - c)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own 2D print runs (Sec. III): Table I inks, unit conversion
+# (Eq. 30-33), the 240 x 880 D2Q9 box. Setup arithmetic only.
+# ---------------------------------------------------------------------------
+
+# Table I, MKS columns: nu_0, nu_inf (m^2/s; the table prints "m^2 s"),
+# lambda (s), n, nu_air (m^2/s); and the LB relaxation time of the air the
+# paper fixed for each ink (tau_B in [0.52, 0.54], Sec. III), read from the
+# table's LB nu_air = c_s^2 (tau_B - 1/2).
+TABLE1 = {
+    "1%-25C": dict(nu0=15.6e-5, nu_inf=2.11e-5, lam=3.16e-3, n=0.751, nu_air=1.552e-5, tau_air=0.54),
+    "2%-25C": dict(nu0=66.7e-5, nu_inf=0.69e-5, lam=5.96e-3, n=0.713, nu_air=1.552e-5, tau_air=0.53),
+    "3%-25C": dict(nu0=463.6e-5, nu_inf=3.64e-5, lam=62.5e-3, n=0.573, nu_air=1.552e-5, tau_air=0.52),
+    "3%-40C": dict(nu0=186.8e-5, nu_inf=5.14e-5, lam=10.2e-3, n=0.737, nu_air=1.552e-5, tau_air=0.52),
+}
+D_NOZZLE_MKS = 0.2e-3     # m, nozzle diameter (Sec. III)
+D_NOZZLE_LB = 60          # lattice nodes
+RHO_AIR_MKS = 1.184       # kg/m^3 at 25 C (the air of Eq. 32)
+RHO_INK_MKS = 1000.0      # kg/m^3: an aqueous alginate solution, in Eq. 30
+DENSITY_RATIO = 842.0     # gamma = rho_Y / rho_B (Sec. III)
+SIGMA_MKS = 50.0e-3       # N/m
+PSI_MKS = 14e-6           # kg/s, the mass flow rate of Eq. 30
+
+
+def lb_units(ink):
+    """Conversion factors of Eq. 31-33 for one Table I ink: dx (m), dt (s),
+    dm (kg). dt follows from the air's LB viscosity c_s^2 (tau_B - 1/2)."""
+    t = TABLE1[ink]
+    dx = D_NOZZLE_MKS / D_NOZZLE_LB
+    nu_air_lb = (t["tau_air"] - 0.5) / 3.0
+    dt = dx * dx * nu_air_lb / t["nu_air"]
+    dm = dx ** 3 * RHO_AIR_MKS / 1.0  # rho^B_LB = 1
+    return dict(dx=dx, dt=dt, dm=dm)
+
+
+def table1_lb(ink):
+    """A Table I ink in lattice units: kinematic viscosities by dt/dx^2, the
+    Cross time lambda / dt (in steps; the table's LB column prints its
+    exponent with the sign flipped), n unchanged, the air's viscosity."""
+    t = TABLE1[ink]
+    u = lb_units(ink)
+    k = u["dt"] / u["dx"] ** 2
+    return dict(nu0=t["nu0"] * k, nu_inf=t["nu_inf"] * k, lam=t["lam"] / u["dt"], n=t["n"],
+                nu_air=t["nu_air"] * k, tau_air=t["tau_air"])
+
+
+def ink_speed_lb(ink):
+    """v_ink of Eq. 30, psi / (rho pi (d/2)^2), in lattice units per step."""
+    u = lb_units(ink)
+    v = PSI_MKS / (RHO_INK_MKS * 3.141592653589793 * (D_NOZZLE_MKS / 2) ** 2)
+    return v * u["dt"] / u["dx"]
+
+
+def paper_print_2d(ink="1%-25C", speed_ratio=1.0, storage="f64", alpha_air=0.2, wall=4.0, shape=(880, 1, 240),
+                   ratio=DENSITY_RATIO):
+    """The paper's 2D print run (Sec. III): D2Q9 box 880 (x, periodic) by 240
+    (z), nozzle diameter 60 and gap 60, nozzle filled with ink at start; the
+    ink a Table I Cross fluid, the air Newtonian at the ink's tau_B; density
+    ratio 842 by phi (Eq. 7-8: gamma = (1 - alpha_B)/(1 - alpha_Y), with
+    alpha_B = alpha_air); sigma = 0.05 N/m converted and A from Eq. 13 at the
+    air's tau; head speed speed_ratio x v_ink. The wall thickness is not given
+    (wall). ratio < 842 gives the same run at a lower density ratio."""
+    nx, ny, nz = shape
+    lb = table1_lb(ink)
+    u = lb_units(ink)
+    v = ink_speed_lb(ink)
+    alpha_ink = 1.0 - (1.0 - alpha_air) / ratio
+    sigma_lb = SIGMA_MKS * u["dt"] ** 2 / u["dm"]
+    A = 9.0 * sigma_lb / (2.0 * lb["tau_air"])
+    return dict(
+        shape=shape,
+        params=dict(velset=0, storage=storage, tau_amb=lb["tau_air"], rho0_ink=float(ratio), rho0_amb=1.0,
+                    alpha_ink=alpha_ink, alpha_amb=alpha_air, A=A, beta=0.7, zeta_ink=1.0, zeta_amb=1.0,
+                    drag_gamma=0.0, drag_height=4.0, body_force=(0.0, 0.0, 0.0)),
+        geom=dict(z_mode=1, top_mode=0, nozzle=1, head_pos=(nx - 90.0, 0.0), head_vel=(-speed_ratio * v, 0.0),
+                  r_inner=D_NOZZLE_LB / 2.0, wall_thickness=wall, gap=60, u_ink=v, top_vel=(0.0, 0.0, 0.0),
+                  rho_top_amb=1.0),
+        rheo=dict(law=1, nu0=lb["nu0"], nu_inf=lb["nu_inf"], lam=lb["lam"], n=lb["n"], K=0.05,
+                  tau_min=min(lb["tau_air"], 0.5 + 3 * lb["nu_inf"]), tau_max=0.5 + 3 * lb["nu0"]),
+        units=u, sigma_lb=sigma_lb,
+    )
