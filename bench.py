@@ -575,24 +575,29 @@ def run_e2e(lat, rY, rB, storage, nsites, args, barrier, max_over_ranks, ws):
     import numpy as np
     import torch
     from paper_2102_02655_gb300 import lbm
-    npd = np.float64 if storage == "f64" else np.float32
     tdt = torch.float64 if storage == "f64" else torch.float32
-    h_rY = torch.from_numpy(rY.astype(npd)).pin_memory()
-    h_rB = torch.from_numpy(rB.astype(npd)).pin_memory()
+    # the request's input is the spun-up print state the headline is timed on
+    # (its densities and velocity, read back untimed into pinned memory), so
+    # that both numbers time the same kind of step
+    mask = lbm.LBM_FIELD_RHO_INK | lbm.LBM_FIELD_RHO_AMB | lbm.LBM_FIELD_U
+    ins = [torch.empty(rY.shape, dtype=tdt).pin_memory() for _ in range(5)]
+    lat.fields(mask=mask, out=[t.numpy() for t in ins])
+    h_u = torch.stack(ins[2:5]).pin_memory()
     outs = [torch.empty(rY.shape, dtype=tdt).pin_memory() for _ in range(5)]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat.set_fields(h_rY.numpy(), h_rB.numpy())
+    lat.set_fields(ins[0].numpy(), ins[1].numpy(), h_u.numpy())
     lat.step(args.steps)
     res = lat.fields(mask=lbm.LBM_FIELD_RHO_INK | lbm.LBM_FIELD_RHO_AMB | lbm.LBM_FIELD_U,
                      out=[o.numpy() for o in outs])
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     esz = 8 if storage == "f64" else 4
     e2e = {"value": aggregate_mlups(ws, nsites, args.steps, e2e_s * 1e3), "unit": "MLUPS",
-           "h2d_bytes_per_step": 2 * nsites * esz / args.steps,
+           "h2d_bytes_per_step": 5 * nsites * esz / args.steps,
            "d2h_bytes_per_step": (5 * nsites * esz + 120) / args.steps,
-           "what": "per request: pinned H2D of rho_ink, rho_amb; K steps; D2H of rho_ink, rho_amb, u, diag"}
+           "what": "per request: pinned H2D of a spun-up state's rho_ink, rho_amb, u; K steps; D2H of rho_ink, "
+                   "rho_amb, u, diag"}
     return e2e, res["diag"]["unstable"]
 
 

@@ -10,7 +10,7 @@ the same values. The file serves the paths that compute in FP32 (FP32 and
 16-bit storage), so the oracle takes their rounding floor for the direction
 of Eq. 16 (2^-16; the oracle's arithmetic stays FP64).
 
-    python tests/golden/make_print_128x64x64_10k.py   # about 30 min on 8 cores
+    python tests/golden/make_print_128x64x64_10k.py   # about 2.5 hours on 4 cores
 """
 import os
 import sys
