@@ -550,8 +550,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
         // (152 SMs), at least 4 planes so the two-plane prologue stays
         // amortised
         const bool fp64 = cfg->storage == LBM_F64;
-        const int th = fused_tile_rows(fp64);
-        const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + th - 1) / th);
+        const long long tiles = (long long)((cfg->nx + 31) / 32) * ((cfg->ny + kFusedTileH - 1) / kFusedTileH);
         long long chunks = (152LL * 4 * fused_ctas_per_sm(fp64) + tiles - 1) / tiles;
         chunks = std::max(1LL, std::min<long long>(chunks, cfg->nz));
         h->zchunk = std::max(4, (int)((cfg->nz + chunks - 1) / chunks));

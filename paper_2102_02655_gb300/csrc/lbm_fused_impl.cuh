@@ -237,16 +237,15 @@ __device__ __forceinline__ void density(const real f[2][19], const StepArgs<real
 // One tile column (x0, y0) of planes [za, zb) of one lattice; shared memory
 // as laid out by fused_smem. Used by the single-lattice kernel (one column
 // per CTA) and by the persistent batched kernel (a list of columns per CTA).
-// The CTA has 32 x 8 threads; each owns R sites of the 32 x 8R tile, at rows
-// ty, ty + 8, ..., so that a thread carries R independent pulls and
-// collisions (instruction-level parallelism) and the halo ring is shared by
-// more sites. The own sites wait for their collision as their 17 moments
+// The CTA has 32 x 8 threads, one site of the 32 x 8 tile each (two sites per
+// thread, on 32 x 16 tiles at two CTAs per SM, measured 20% slower). The own
+// sites wait for their collision as their 17 moments
 // (see moments()) rather than their 38 populations: less than half the
 // shared memory and none of the populations' registers across the plane.
-template <typename real, typename S, bool kUnit, int R>
+template <typename real, typename S, bool kUnit>
 __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned char* smraw, int x0, int y0, int za,
                                              int zb) {
-    using T = Tile<8 * R, 32>;
+    using T = Tile<8, 32>;
     constexpr int NT = T::NT, HX = T::HX, HY = T::HY, HS = T::HS;
     constexpr int NRING = T::NRING, SX = T::SX, SY = T::SY, SS = T::SS;
     constexpr int NTH = 256;                        // threads
@@ -281,38 +280,29 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     };
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    int xs[R], ys[R], gxs[R], gys[R], hidx[R];
-    bool in_xy[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        xs[r] = x0 + tx;
-        ys[r] = y0 + ty + 8 * r;
-        in_xy[r] = xs[r] < p.nx && ys[r] < p.ny;
-        gxs[r] = in_xy[r] ? xs[r] : wrapn(xs[r], p.nx);
-        gys[r] = in_xy[r] ? ys[r] : wrapn(ys[r], p.ny);
-        hidx[r] = (ty + 8 * r + 1) * HX + (tx + 1);
-    }
+    // the own site: (xs, ys), periodic image (gxs, gys), colour-ring index hidx
+    const int xs = x0 + tx, ys = y0 + ty;
+    const bool in_xy = xs < p.nx && ys < p.ny;
+    const int gxs = in_xy ? xs : wrapn(xs, p.nx), gys = in_xy ? ys : wrapn(ys, p.ny);
+    const int hidx = (ty + 1) * HX + (tx + 1);
     // the nozzle box's column test, once per column (its planes per plane)
-    bool box_xy[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) box_xy[r] = in_box_xy(p, xs[r], ys[r]);
+    const bool box_xy = in_box_xy(p, xs, ys);
     double bc[2] = {0.0, 0.0};
 
-    // Densities after streaming on plane zz for the tile (items 0 .. R-1, the
-    // own sites) and its halo ring (item R), and with outer also the second
-    // ring (item R + 1, the substrate prologue). The own sites' moments go to
+    // Densities after streaming on plane zz for the tile (item 0, the own
+    // sites) and its halo ring (item 1), and with outer also the second ring
+    // (item 2, the substrate prologue). The own sites' moments go to
     // buffer zz & 1 and their boundary-link mass is booked once, for this
     // chunk's planes. One pull body serves every item.
     auto load_plane = [&](int zz, bool keep, bool outer) {
-        const int nitems = R + (outer ? 2 : 1);
+        const int nitems = outer ? 3 : 2;
         for (int it = 0; it < nitems; ++it) {
             int hx, hy;  // coordinates in the tile grown by two rings
-            int r = -1;
-            if (it < R) {
-                r = it;
+            const bool own = it == 0;
+            if (own) {
                 hx = tx + 2;
-                hy = ty + 8 * r + 2;
-            } else if (it == R) {
+                hy = ty + 2;
+            } else if (it == 1) {
                 if (tid >= NRING) continue;
                 ring_coord<HX, HY>(tid, &hx, &hy);
                 hx += 1;
@@ -326,12 +316,10 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                 else { const int k = j - 2 * SX; hy = 1 + (k >> 1); hx = (k & 1) ? SX - 1 : 0; }
             }
             const int px = wrapn(x0 - 2 + hx, p.nx), py = wrapn(y0 - 2 + hy, p.ny);
-            const bool own = r >= 0;
-            real* dst = own && keep ? pops + (zz & 1) * NS * NT + tid + NTH * r : nullptr;
+            real* dst = own && keep ? pops + (zz & 1) * NS * NT + tid : nullptr;
             real rY, rB;
             if (zz == p.nz - 1) {
-                const bool led = own && keep && in_xy[r < 0 ? 0 : r] && zz < zb &&
-                                 !in_box(p, xs[r < 0 ? 0 : r], ys[r < 0 ? 0 : r], zz);
+                const bool led = own && keep && in_xy && zz < zb && !in_box(p, xs, ys, zz);
                 real ft[2][19];
                 const TopPull<real> res = pull_top<S>(p, px, py, ft, led);
                 if (dst) stage(dst, ft, &rY, &rB);
@@ -349,13 +337,12 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                 sub[hy * SX + hx] = rY;
                 sub[SS + hy * SX + hx] = rB;
             }
-            if (it <= R) C.put(p, slot_of(zz), (hy - 1) * HX + (hx - 1), rY, rB);
+            if (it <= 1) C.put(p, slot_of(zz), (hy - 1) * HX + (hx - 1), rY, rB);
         }
     };
 
-    // Plane zz below the top (1 <= zz <= nz - 2): the own sites' pulls are
-    // issued together (R independent memory round trips in flight), then the
-    // halo site's.
+    // Plane zz below the top (1 <= zz <= nz - 2): the own site's pull, then
+    // (warps 0-2) the halo site's.
     const bool has_halo = tid < NRING;
     int rx = 0, ry = 0;
     if (has_halo) ring_coord<HX, HY>(tid, &rx, &ry);
@@ -372,19 +359,13 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         real rY, rB;
         const real* rs[3] = {refs + ((zz - 1) & 3) * SS, refs + (zz & 3) * SS, refs + ((zz + 1) & 3) * SS};
         {
-            real f[R][2][19];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if constexpr (kRef)
-                    pull_interior<S, real, SX>(p, gxs[r], gys[r], zz, f[r], rs, (ty + 8 * r + 2) * SX + tx + 2);
-                else
-                    pull_interior<S>(p, gxs[r], gys[r], zz, f[r]);
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                stage(pops + (zz & 1) * NS * NT + tid + NTH * r, f[r], &rY, &rB);
-                C.put(p, slot_of(zz), hidx[r], rY, rB);
-            }
+            real f[2][19];
+            if constexpr (kRef)
+                pull_interior<S, real, SX>(p, gxs, gys, zz, f, rs, (ty + 2) * SX + tx + 2);
+            else
+                pull_interior<S>(p, gxs, gys, zz, f);
+            stage(pops + (zz & 1) * NS * NT + tid, f, &rY, &rB);
+            C.put(p, slot_of(zz), hidx, rY, rB);
         }
         if (has_halo) {
             real h[2][19];
@@ -449,15 +430,13 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
         __syncthreads();
         // open top: zero normal gradient, the ghost plane above is the top plane
         const int sup = z + 1 < p.nz ? slot_of(z + 1) : slot_of(z);
-        // the own sites that belong to this kernel (not outside the lattice,
+        // the own site if it belongs to this kernel (not outside the lattice,
         // not in the nozzle box, whose sites pull from wall nodes here)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (!in_xy[r] || (box_xy[r] && z >= p.box.z0 && z < p.box.z1)) continue;
-            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx[r]};
+        if (in_xy && !(box_xy && z >= p.box.z0 && z < p.box.z1)) {
+            SmemNb<real, kUnit, HX, HS> nb{C.col, {slot_of(z - 1), slot_of(z), sup}, hidx};
             SiteOut<real> so;
-            const int s = z * (int)p.plane + gys[r] * p.nx + gxs[r];
-            const real* b = pops + (z & 1) * NS * NT + tid + NTH * r;
+            const int s = z * (int)p.plane + gys * p.nx + gxs;
+            const real* b = pops + (z & 1) * NS * NT + tid;
             Moments<real> M;
             M.rY = b[0];
             M.sd = b[NT];
@@ -474,7 +453,7 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
                                             });
             ref_put<S>(p, s, so.cY);
             if (z >= p.nz - 2)
-                for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, xs[r], ys[r], z)] = so.u[a];
+                for (int a = 0; a < 3; ++a) p.u_cur[utop_idx(p, a, xs, ys, z)] = so.u[a];
             if (unstable_site(so.rhoY, so.rhoB)) bad = 1;
             if (p.write_fields) {
                 real* F = p.fields;
@@ -508,19 +487,16 @@ __device__ __forceinline__ void fused_column(const StepArgs<real>& p, unsigned c
     if (bad) atomicOr(p.flags, 1);
 }
 
-template <typename real, typename S, bool kUnit, int R>
+template <typename real, typename S, bool kUnit>
 constexpr size_t fused_smem() {
-    using T = Tile<8 * R, 32>;
+    using T = Tile<8, 32>;
     return sizeof(real) * (2 * 17 * T::NT + 4 * Colour<real, kUnit, T::HS>::NV * T::HS +
                            (Stored<S>::kDev ? 4 * T::SS : 0));
 }
 
 // Configuration of the single-lattice bulk kernel: one site per thread
 // (32 x 8 tiles), three CTAs of 256 threads per SM in FP32 arithmetic (80
-// registers), one in FP64. (Two sites per thread, 32 x 16 tiles at two CTAs
-// per SM, measured 20% slower on the print lattice.)
-template <typename real>
-constexpr int fused_rows() { return 1; }
+// registers), one in FP64.
 template <typename real>
 constexpr int fused_minb() { return sizeof(real) == 8 ? 1 : 3; }
 constexpr int kTileH = 8;  // rows of the batched kernel's tiles (one site per thread)
@@ -528,10 +504,9 @@ constexpr int kTileH = 8;  // rows of the batched kernel's tiles (one site per t
 template <typename real, typename S, bool kUnit>
 __global__ void __launch_bounds__(256, fused_minb<real>()) k_fused(StepArgs<real> p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int R = fused_rows<real>();
     const int n = z_chunks(p.nz, zchunk);
-    fused_column<real, S, kUnit, R>(p, smraw, blockIdx.x * 32, blockIdx.y * 8 * R, z_chunk_begin(p.nz, n, blockIdx.z),
-                                    z_chunk_begin(p.nz, n, blockIdx.z + 1));
+    fused_column<real, S, kUnit>(p, smraw, blockIdx.x * 32, blockIdx.y * 8, z_chunk_begin(p.nz, n, blockIdx.z),
+                                 z_chunk_begin(p.nz, n, blockIdx.z + 1));
 }
 
 // Persistent form over many lattices: the CTAs take columns of the work list
@@ -568,7 +543,7 @@ __global__ void __launch_bounds__(Tile<kTileH>::NT, batch_minb<real>())
             last = it.x;
             __syncthreads();
         }
-        fused_column<real, S, kUnit, 1>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
+        fused_column<real, S, kUnit>(sp, smraw, it.y & 0xffff, it.y >> 16, it.z, it.w);
     }
 }
 
@@ -585,13 +560,12 @@ void set_smem_once(K kernel, size_t smem, unsigned* configured) {
 
 template <typename real, typename S, bool kUnit>
 int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
-    constexpr int R = fused_rows<real>();
-    constexpr size_t smem = fused_smem<real, S, kUnit, R>();
+    constexpr size_t smem = fused_smem<real, S, kUnit>();
     static_assert(smem * fused_minb<real>() <= 227 * 1024, "CTAs per SM");
     static unsigned configured = 0;
     set_smem_once(k_fused<real, S, kUnit>, smem, &configured);
     dim3 block(32, 8);
-    dim3 grid((p.nx + 31) / 32, (p.ny + 8 * R - 1) / (8 * R), z_chunks(p.nz, zchunk));
+    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, z_chunks(p.nz, zchunk));
     k_fused<real, S, kUnit><<<grid, block, smem, st>>>(p, zchunk);
     return 1;
 }
@@ -599,7 +573,7 @@ int launch_one(const StepArgs<real>& p, int zchunk, cudaStream_t st) {
 template <typename real, typename S, bool kUnit>
 int launch_batch_one(const StepArgs<real>* args, const int4* items, int n_items, int* queue, int grid,
                      cudaStream_t st, int* occupancy) {
-    constexpr size_t smem = fused_smem<real, S, kUnit, 1>();
+    constexpr size_t smem = fused_smem<real, S, kUnit>();
     static unsigned configured = 0;
     set_smem_once(k_fused_batch<real, S, kUnit>, smem, &configured);
     if (occupancy) {

@@ -46,9 +46,8 @@ int launch_fused_batch(const StepArgs<real>* args, const int4* items, int n_item
                        cudaStream_t st, int* occupancy);
 // tile height (sites in y) of the batched fused kernel's 32-wide column tiles
 constexpr int kFusedTileH = 8;
-// tile height and resident CTAs per SM of the single-lattice fused kernel:
-// 32 x 8 tiles, three CTAs per SM in FP32 arithmetic, one in FP64
-inline int fused_tile_rows(bool) { return 8; }
+// resident CTAs per SM of the single-lattice fused kernel (32 x 8 tiles):
+// three in FP32 arithmetic, one in FP64
 inline int fused_ctas_per_sm(bool fp64) { return fp64 ? 1 : 3; }
 
 // Batched phase-by-phase step of the nozzle boxes of many lattices: one
