@@ -7,6 +7,7 @@ way, to see it settle), its coverage ratio and largest pressure variation over
 the whole thread, and POI (paper_2102_02655_gb300.poi).
 
     python -m paper_2102_02655_gb300.paper2d --ink 1%-25C --speed 1.0 [--storage f64] [--ratio 842]
+        [--alpha-air 0.2] [--a-scale 1] [--beta 0.7]
 
 prints one JSON line per run. The fields are read back every --every steps
 (the touch is detected at that granularity)."""
@@ -20,9 +21,15 @@ from . import inputs as I
 from . import lbm, poi
 
 
-def run(ink, speed, storage="f64", every=1000, max_steps=3_000_000, travel_d=6.0, device=0, ratio=I.DENSITY_RATIO):
+def run(ink, speed, storage="f64", every=1000, max_steps=3_000_000, travel_d=6.0, device=0, ratio=I.DENSITY_RATIO,
+        alpha_air=0.2, a_scale=1.0, beta=None):
+    """One run; alpha_air, a_scale (a factor on the A that Eq. 13 gives) and
+    beta change the choices the paper does not print."""
     import torch
-    w = I.paper_print_2d(ink, speed_ratio=speed, storage=storage, ratio=ratio)
+    w = I.paper_print_2d(ink, speed_ratio=speed, storage=storage, ratio=ratio, alpha_air=alpha_air)
+    w["params"]["A"] *= a_scale
+    if beta is not None:
+        w["params"]["beta"] = beta
     shape = w["shape"]
     nx, _, nz = shape
     g = w["geom"]
@@ -58,7 +65,8 @@ def run(ink, speed, storage="f64", every=1000, max_steps=3_000_000, travel_d=6.0
                 break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    out = dict(ink=ink, speed_ratio=speed, density_ratio=ratio, storage=storage, shape=shape, steps=n, status=status,
+    out = dict(ink=ink, speed_ratio=speed, density_ratio=ratio, alpha_air=alpha_air, A=w["params"]["A"],
+               beta=w["params"]["beta"], storage=storage, shape=shape, steps=n, status=status,
                mlups=nx * nz * n / wall / 1e6, wall_s=wall, v_ink_lb=g["u_ink"], touch_step=touch)
     if touch is not None and status == "done":
         pp = f["p"][:, 0, :]
@@ -79,8 +87,12 @@ def main():
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--ratio", type=float, default=I.DENSITY_RATIO, help="density ratio (the paper's: 842)")
+    ap.add_argument("--alpha-air", type=float, default=0.2, help="alpha_B (not given in the paper)")
+    ap.add_argument("--a-scale", type=float, default=1.0, help="factor on A from Eq. 13")
+    ap.add_argument("--beta", type=float, default=None, help="recolouring beta (default 0.7)")
     a = ap.parse_args()
-    res = [run(a.ink, s, a.storage, a.every, a.max_steps, ratio=a.ratio) for s in a.speed]
+    res = [run(a.ink, s, a.storage, a.every, a.max_steps, ratio=a.ratio, alpha_air=a.alpha_air, a_scale=a.a_scale,
+               beta=a.beta) for s in a.speed]
     ok = [r for r in res if r.get("poi")]
     if ok:
         for r, v in zip(ok, poi.normalised([r["poi"] for r in ok])):
