@@ -198,3 +198,31 @@ def test_print_128x64x64_horizon(horizon_errors, storage, horizon):
     if bad:
         pytest.xfail("%s after %d steps over %.0e: %s" % (storage, horizon, BAR[storage],
                                                          {k: "%.2e" % v for k, v in bad.items()}))
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "f32"])
+@pytest.mark.parametrize("shape", [(1, 1, 5), (2, 3, 4), (5, 3, 7), (33, 9, 3)])
+def test_tiny_lattices_fused(shape, storage):
+    """Lattices narrower than one tile and its rings, and nz = 3: the fused
+    kernel's periodic images, its colour ring and (16-bit) its ring of
+    source ink fractions wrap onto the same few sites. 25 steps against the
+    oracle at the storage's bar."""
+    lbm = _lbm()
+    nx, ny, nz = shape
+    rY = np.zeros((nz, ny, nx))
+    rY[nz // 2] = 0.5
+    rY[max(0, nz // 2 - 1)] += 0.2
+    params = dict(velset=1, storage=storage)
+    geom = dict(nozzle=0, z_mode=O.Z_WALLS, top_mode=O.TOP_OPEN, rho_top_amb=1.01)
+    rheo = dict(law=O.POWER_LAW, n=0.6, K=0.05, tau_min=0.51, tau_max=2.0)
+    ref = O.Oracle(shape, params=params, geom=geom, rheo=rheo)
+    ref.set_fields(rY, 1.0 - rY)
+    ref.step(25)
+    lat = lbm.Lattice(shape, params, geom, rheo, path="fused")
+    lat.set_fields(rY, 1.0 - rY)
+    lat.step(25)
+    fg = lat.fields()
+    lat.close()
+    e = field_errors(fg, ref.fields(), HYDRO + ("rhoN",))
+    bar = TOL16 if storage == "f16dev" else 1e-5
+    assert max(e.values()) <= bar, (shape, storage, e)
