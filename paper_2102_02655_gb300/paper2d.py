@@ -7,7 +7,7 @@ way, to see it settle), its coverage ratio and largest pressure variation over
 the whole thread, and POI (paper_2102_02655_gb300.poi).
 
     python -m paper_2102_02655_gb300.paper2d --ink 1%-25C --speed 1.0 [--storage f64] [--ratio 842]
-        [--alpha-air 0.2] [--a-scale 1] [--beta 0.7]
+        [--alpha-air 0.2] [--a-scale 1] [--beta 0.7] [--drag 0]
 
 prints one JSON line per run. The fields are read back every --every steps
 (the touch is detected at that granularity)."""
@@ -22,12 +22,14 @@ from . import lbm, poi
 
 
 def run(ink, speed, storage="f64", every=1000, max_steps=3_000_000, travel_d=6.0, device=0, ratio=I.DENSITY_RATIO,
-        alpha_air=0.2, a_scale=1.0, beta=None):
-    """One run; alpha_air, a_scale (a factor on the A that Eq. 13 gives) and
-    beta change the choices the paper does not print."""
+        alpha_air=0.2, a_scale=1.0, beta=None, drag=0.0):
+    """One run; alpha_air, a_scale (a factor on the A that Eq. 13 gives),
+    beta and the substrate friction gamma of Eq. 29 (drag) change the choices
+    the paper does not print."""
     import torch
     w = I.paper_print_2d(ink, speed_ratio=speed, storage=storage, ratio=ratio, alpha_air=alpha_air)
     w["params"]["A"] *= a_scale
+    w["params"]["drag_gamma"] = drag
     if beta is not None:
         w["params"]["beta"] = beta
     shape = w["shape"]
@@ -66,7 +68,7 @@ def run(ink, speed, storage="f64", every=1000, max_steps=3_000_000, travel_d=6.0
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     out = dict(ink=ink, speed_ratio=speed, density_ratio=ratio, alpha_air=alpha_air, A=w["params"]["A"],
-               beta=w["params"]["beta"], storage=storage, shape=shape, steps=n, status=status,
+               beta=w["params"]["beta"], drag_gamma=drag, storage=storage, shape=shape, steps=n, status=status,
                mlups=nx * nz * n / wall / 1e6, wall_s=wall, v_ink_lb=g["u_ink"], touch_step=touch)
     if touch is not None and status == "done":
         pp = f["p"][:, 0, :]
@@ -90,9 +92,10 @@ def main():
     ap.add_argument("--alpha-air", type=float, default=0.2, help="alpha_B (not given in the paper)")
     ap.add_argument("--a-scale", type=float, default=1.0, help="factor on A from Eq. 13")
     ap.add_argument("--beta", type=float, default=None, help="recolouring beta (default 0.7)")
+    ap.add_argument("--drag", type=float, default=0.0, help="friction gamma of Eq. 29 within 4 nodes of the substrate")
     a = ap.parse_args()
     res = [run(a.ink, s, a.storage, a.every, a.max_steps, ratio=a.ratio, alpha_air=a.alpha_air, a_scale=a.a_scale,
-               beta=a.beta) for s in a.speed]
+               beta=a.beta, drag=a.drag) for s in a.speed]
     ok = [r for r in res if r.get("poi")]
     if ok:
         for r, v in zip(ok, poi.normalised([r["poi"] for r in ok])):
